@@ -1,0 +1,354 @@
+"""Benchmark: solid Newton steps per second on the two-layer artery tube.
+
+Workload (per GPU): artery tube, inner radius 1.0, media 0.13 (4 element
+layers), adventitia 0.10 (4 layers), length 8, 64 x 8 x 128 hexahedra x 6
+tetrahedra = 393,216 elements, 74,304 nodes, 297,216 unknowns; c10 = 3.0 /
+0.3, k1 = 2.3 / 0.56, k2 = 0.84 / 0.71, fibres at +-29 / +-62 degrees,
+kappa = 1e3 c10 (media); ends fixed axially; internal pressure ramped
+0 -> 1.6 in 10 load steps (synthetic, seeded geometry: no dataset).
+
+One bench step = one call of fsi_solid_newton_step: FP64 residual, tangent
+assembly, numeric AMG set-up, FGMRES + AMG V-cycle to a relative residual of
+1e-8, update.  The load advances when a step starts from a converged state;
+after the last load step the ramp restarts from the reference state.  The
+matrix, hierarchy and Krylov basis (~1 GB) are far larger than the 129 MB L2,
+so no explicit flush is done between steps.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solid Newton steps/s (assemble+AMG-Krylov to 1e-8)"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP64_PEAK_TFLOPS = 1.196      # project-measured dependent-FMA rate on this GB300 (FP64 pipe)
+N_LOADS = 10
+P_MAX = 1.6
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def workload_mesh(nz=128):
+    from fixtures import artery_layers, artery_tube
+    return artery_tube(n_theta=64, n_media=4, n_adv=4, n_z=nz, length=8.0 * nz / 128,
+                       materials=artery_layers(1.0e3))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def start(self):
+        def run():
+            q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                         timeout=5).stdout.strip()
+                    if out:
+                        self.samples.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._thr = threading.Thread(target=run, daemon=True)
+        self._thr.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._thr:
+            self._thr.join(timeout=10)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if "Active" in s[2 + k]
+                          and "Not" not in s[2 + k]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def jacobi0_bytes(n, nb, fp32):
+    """Algorithmic bytes of one finest-level damped block-Jacobi sweep:
+    4x4 values + column index per block, row pointer, x / b / y vectors and
+    the 4x4 inverse per block row."""
+    vb = 4 if fp32 else 8
+    return nb * (16 * vb + 4) + (n + 1) * 4 + n * (3 * 4 * vb + 16 * vb)
+
+
+class RampDriver:
+    """Advances the pressure ramp between Newton steps."""
+
+    def __init__(self, solver, n, torch):
+        from paper_1312_5561_gb300.binding import Load
+        self.Load = Load
+        self.solver = solver
+        self.torch = torch
+        self.state = torch.zeros((n, 4), device="cuda", dtype=torch.float64)
+        self.k = 1
+        self.r0 = None
+        self.newton_in_load = 0
+
+    def step(self, state=None):
+        st = self.state if state is None else state
+        info = self.solver.newton_step(st, self.Load(pressure=P_MAX * self.k / N_LOADS), check=False)
+        if info.status not in (0, -5):
+            raise RuntimeError(f"newton_step failed with status {info.status}")
+        if self.r0 is None:
+            self.r0 = info.res0
+        self.newton_in_load += 1
+        if info.res0 <= 1e-8 * self.r0 or self.newton_in_load > 12:
+            self.k += 1
+            self.r0 = None
+            self.newton_in_load = 0
+            if self.k > N_LOADS:
+                self.k = 1
+                st.zero_()
+        return info
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1312_5561_gb300.binding import SolidSolver, launch_count
+    torch.cuda.set_device(args.local_rank)
+    mesh = workload_mesh(args.nz)
+    prec = 1 if args.precision == "fp32" else 0
+    solver = SolidSolver(mesh, precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, max_krylov=600)
+    levels = solver.levels()
+    drv = RampDriver(solver, mesh.n_nodes, torch)
+    for _ in range(args.warmup):
+        drv.step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    solver.kernel_timing(True)
+    l0 = launch_count()
+    clocks = ClockSampler(args.local_rank)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    krylov = 0
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        info = drv.step()
+        krylov += info.krylov_its_last
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = launch_count() - l0
+    ms_total = ev0.elapsed_time(ev1)
+    prof = solver.kernel_timing(False)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    steps_per_s = args.steps / (ms_total * 1e-3)
+
+    # element tangents / s (residual + tangent assembly, device resident)
+    st = drv.state
+    for _ in range(2):
+        solver.residual_tangent(st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        solver.residual_tangent(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tangents_per_s = mesh.n_elems * reps / (e0.elapsed_time(e1) * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    host = torch.zeros((mesh.n_nodes, 4), dtype=torch.float64).pin_memory()
+    host.copy_(drv.state.cpu())
+    dev = torch.empty_like(drv.state)
+    e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        dev.copy_(host, non_blocking=True)
+        drv.step(dev)
+        host.copy_(dev, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e = e_steps / (time.perf_counter() - t0)
+    nbytes = mesh.n_nodes * 4 * 8
+
+    L0n, L0nb = levels[0]
+    dominant = max(prof, key=lambda k: prof[k][0])
+    peaks, src = _peaks()
+    roof = None
+    jt, jc = prof["jacobi0"]
+    if jc > 0:
+        per_launch_s = jt * 1e-3 / jc
+        byt = jacobi0_bytes(L0n, L0nb, prec == 1)
+        ach = byt / per_launch_s / 1e9
+        roof = {"kernel": "bsr_kernel<...,4,4,MODE=2> (finest-level block-Jacobi sweep)", "bound": "hbm",
+                "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm_gbs"], 3), "traffic": None, "peak_source": src,
+                "bytes_per_launch": int(byt), "avg_launch_us": round(per_launch_s * 1e6, 2)}
+    return {
+        "steps_per_s": steps_per_s, "ms_per_step": ms_total / args.steps, "tangents_per_s": tangents_per_s,
+        "e2e_steps_per_s": e2e, "bytes": nbytes, "launches": launches, "clocks": clk,
+        "prof": {k: [round(v[0], 3), v[1]] for k, v in prof.items()}, "dominant": dominant, "roofline": roof,
+        "krylov_per_step": krylov / args.steps, "levels": levels, "n_elems": mesh.n_elems,
+        "n_nodes": mesh.n_nodes,
+    }
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import scipy.sparse.linalg as spla
+from fixtures import artery_layers, artery_tube
+from oracle import solid as O
+nz, steps, warm = {nz}, {steps}, {warm}
+mesh = artery_tube(n_theta=64, n_z=nz, length=8.0 * nz / 128, materials=artery_layers(1.0e3))
+P = O.Problem(mesh)
+state = np.zeros((mesh.n_nodes, 4))
+fext = P.external_force(0.16)
+times = []
+for k in range(warm + steps):
+    t0 = time.perf_counter()
+    R = P.residual(state, fext)
+    K = P.tangent(state)
+    dv = spla.spsolve(K.tocsc(), -R.ravel())
+    state = state + dv.reshape(-1, 4)
+    times.append(time.perf_counter() - t0)
+idx = np.arange(min(mesh.n_elems, 4096))
+t0 = time.perf_counter(); P.element_tangents(state, idx); tt = time.perf_counter() - t0
+print(json.dumps({{"n_elems": mesh.n_elems, "step_s": float(np.mean(times[warm:])), "tangent_s": tt / len(idx)}}))
+"""
+
+
+def run_oracle(nz_sample, steps, warm):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_SNIPPET.format(root=ROOT, nz=nz_sample, steps=steps, warm=warm)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_line(args, full_elems, nz_sample, steps, warm):
+    r = run_oracle(nz_sample, steps, warm)
+    scale = full_elems / r["n_elems"]
+    value = 1.0 / (r["step_s"] * scale)
+    return {
+        "value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+        "sample": (f"FP64 oracle Newton step (complex-step tangent, scipy sparse direct solve) on the first "
+                   f"{r['n_elems']} elements (64x8x{nz_sample} slab) of the workload tube, time scaled by "
+                   f"{scale:.0f} to the full mesh"),
+        "tangents_per_s": 1.0 / r["tangent_s"],
+    }
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--nz", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    args.local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    full_elems = 64 * 8 * args.nz * 6
+    config = {"workload": f"two-layer artery tube 64x8x{args.nz} hex x6 tets ({full_elems} tets), kappa=1e3*c10, "
+                          f"pressure ramp 0->1.6 in 10 load steps", "mesh_elems": full_elems,
+              "l2": "inputs larger than L2 (matrix + AMG hierarchy + Krylov basis ~1 GB)", "parallelism": "replicas"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        nz_s = 4
+        line = oracle_line(args, full_elems, nz_s, max(1, args.steps // 10), 1)
+        ms = 1e3 / line["value"]
+        out = {"impl": "reference", "metric": METRIC, "value": line["value"], "unit": "steps/s",
+               "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": config,
+               "cpu_baseline": {k: line[k] for k in ("value", "unit", "cores", "kind", "sample")},
+               "e2e": {"value": line["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_gpu(args, rank, world)
+    other = None
+    if args.precision == "fp32":
+        a2 = argparse.Namespace(**vars(args))
+        a2.precision = "fp64"
+        a2.steps = max(5, args.steps // 2)
+        other = run_gpu(a2, rank, world)
+    if rank != 0:
+        return
+    value = res["steps_per_s"] * world
+    out = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": dict(config, precision=("FP32 tangent + FP32 V-cycle under FP64 residual / outer FGMRES"
+                                          if args.precision == "fp32" else "FP64 throughout"),
+                       krylov_its_per_step=round(res["krylov_per_step"], 1), amg_levels=res["levels"]),
+        "element_tangents_per_s": res["tangents_per_s"] * world,
+        "e2e": {"value": res["e2e_steps_per_s"] * world, "unit": "steps/s",
+                "h2d_bytes_per_step": res["bytes"], "d2h_bytes_per_step": res["bytes"]},
+        "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": res["roofline"],
+        "kernel_ms": res["prof"], "dominant_kernel_class": res["dominant"],
+    }
+    if other is not None:
+        out["plain_fp64"] = {"value": other["steps_per_s"] * world, "ms_per_step": other["ms_per_step"],
+                             "element_tangents_per_s": other["tangents_per_s"] * world,
+                             "krylov_its_per_step": round(other["krylov_per_step"], 1),
+                             "speedup_vs_plain_fp64": res["steps_per_s"] / other["steps_per_s"],
+                             "roofline": other["roofline"], "dominant_kernel_class": other["dominant"]}
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            out["cpu_baseline"] = oracle_line(args, full_elems, 4, 2, 1)
+        except Exception as e:  # the GPU number stands without it
+            out["cpu_baseline"] = {"error": str(e)[-300:]}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

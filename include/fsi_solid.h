@@ -1,0 +1,231 @@
+/*
+ * fsi_solid.h -- C ABI of the GB300 solid Newton step.
+ *
+ * The library solves the structure sub-problem of the partitioned FSI method
+ * of Langer & Yang (arXiv:1312.5561): the residual-stabilised equal-order
+ * P1/P1 displacement-pressure formulation of a nearly incompressible
+ * hyperelastic solid (Sec. 3.2 strong form, Sec. 4.2.3 weak form, Eq. stelas
+ * PSPG term), linearised by Newton's method (Sec. 4.4, Eq. linsys / globsys)
+ * and solved by a Krylov method preconditioned by an aggregation AMG V-cycle
+ * (Sec. 5.4-5.5 describe the paper's own Krylov/AMG solvers).
+ *
+ * Conventions shared by every call:
+ *  - Unknowns are ordered per node as (d_x, d_y, d_z, p): "state" arrays are
+ *    FP64 [n_nodes][4], row-major, on the device, owned by the caller.
+ *  - Host descriptors (mesh, materials, options) are copied at create time;
+ *    the caller keeps ownership of them.
+ *  - All device work is enqueued on the CUDA stream passed as `stream`
+ *    (a cudaStream_t cast to void*; NULL = the legacy default stream).  Every
+ *    call returns after its work has finished on that stream (the status it
+ *    returns is final).
+ *  - A call never exits, aborts or traps; errors come back as fsi_status and
+ *    fsi_solid_last_error() returns a one-line description.
+ *  - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef FSI_SOLID_H
+#define FSI_SOLID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsi_solid_s* fsi_solid_t;   /* opaque, owned by the library */
+
+typedef enum {
+  FSI_OK = 0,
+  FSI_ERR_ARG = -1,            /* invalid argument (NULL, size, index out of range) */
+  FSI_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+  FSI_ERR_OOM = -3,            /* device allocation failed */
+  FSI_ERR_INVERTED = -4,       /* an element reached J <= 0 or a non-finite value */
+  FSI_ERR_NOT_CONVERGED = -5,  /* Newton or Krylov hit its iteration cap */
+  FSI_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
+  FSI_ERR_BOUNDS = -7          /* a bounds-checked gather/scatter index was invalid */
+} fsi_status;
+
+/* Material models (Sec. 2.3.1 and 2.3.2). */
+enum { FSI_MODEL_MOONEY_RIVLIN = 0, FSI_MODEL_ARTERY = 1 };
+
+/* Mesh description (host arrays, copied at create time).
+ *  X         [n_nodes][3]  reference coordinates
+ *  tets      [n_elems][4]  vertex ids, positively oriented (det > 0)
+ *  mat_id    [n_elems]     index into the material table
+ *  fibre     [n_elems][2][3] unit fibre directions a01, a02 (Eq. arinv46), or
+ *                          NULL when no element uses the artery model
+ *  dir_mask  [n_nodes][4]  1 = Dirichlet-constrained component (Eq. elasbnd)
+ *  neu_faces [n_faces][3]  boundary triangles carrying the dead pressure load;
+ *                          the right-hand normal (x1-x0)x(x2-x0) points out
+ *  seg_node  [n_nodes]     segment id (batched independent meshes) or NULL */
+typedef struct {
+  int32_t n_nodes;
+  int32_t n_elems;
+  const double* X;
+  const int32_t* tets;
+  const int32_t* mat_id;
+  const double* fibre;
+  const uint8_t* dir_mask;
+  int32_t n_faces;
+  const int32_t* neu_faces;
+  int32_t n_segments;
+  const int32_t* seg_node;
+} fsi_mesh_desc;
+
+/* One material (Eq. mmreng for Mooney-Rivlin; Eq. areng for the artery).
+ * Mooney-Rivlin uses c10, c01; the artery uses c10, k1, k2.  kappa is the bulk
+ * modulus, rho the reference density (used only when inertia_coef > 0). */
+typedef struct {
+  int32_t model;
+  double c10, c01, k1, k2, kappa, rho;
+} fsi_material;
+
+enum { FSI_PREC_FP64 = 0, FSI_PREC_FP32_IR = 1 };
+enum { FSI_KRYLOV_FGMRES = 0, FSI_KRYLOV_BICGSTAB = 1 };
+enum { FSI_SMOOTHER_JACOBI = 0, FSI_SMOOTHER_CHEBYSHEV = 1 };
+
+/* Solver options.  Defaults come from fsi_solid_default_opts(). */
+typedef struct {
+  int32_t precision;        /* FSI_PREC_*: FP64 throughout, or FP32 tangent and
+                               V-cycle under an FP64 residual / outer Krylov */
+  int32_t krylov;           /* FSI_KRYLOV_* */
+  int32_t restart;          /* FGMRES restart length m (<= 128) */
+  int32_t max_krylov;       /* cap on Krylov iterations per linear solve */
+  int32_t max_newton;       /* cap on Newton iterations per solve */
+  int32_t smoother;         /* FSI_SMOOTHER_* */
+  int32_t nu_pre, nu_post;  /* smoothing sweeps before / after the coarse correction */
+  int32_t cheb_degree;      /* Chebyshev polynomial degree */
+  int32_t coarse_max_nodes; /* stop coarsening when every component is this small */
+  int32_t max_levels;       /* cap on AMG levels */
+  int32_t use_pspg;         /* 1: PSPG term W_s of Eq. stelas on; 0: off */
+  int32_t adaptive_tol;     /* 1: inner tolerance eps_1,k = eps_2,k-1^2 (Sec. 4.4) */
+  int32_t use_graphs;       /* 1: capture the V-cycle in a CUDA graph */
+  int32_t pad0;
+  double omega;             /* block-Jacobi damping */
+  double newton_rtol;       /* stop when ||R(v_k)|| <= newton_rtol ||R(v_0)|| */
+  double krylov_rtol;       /* relative residual reduction of each linear solve */
+  double fibre_factor;      /* 2: S = 2 dPsi/dC; 1: the factor printed in Eq. arpkt */
+  double inertia_coef;      /* 1/(beta dt^2) of the Newmark-beta scheme; 0 = quasi-static */
+} fsi_solver_opts;
+
+/* Load of one solve (device arrays owned by the caller; NULL = absent).
+ *  dir_values    [n_nodes][4] prescribed values written into the constrained
+ *                components of the state before Newton starts (Sec. 4.2.3:
+ *                increments vanish on the Dirichlet boundary)
+ *  pressure      scale of the dead pressure on neu_faces (traction -P n)
+ *  node_pressure [n_nodes] nodal pressure values P_b (P1-interpolated on faces)
+ *  face_pressure [n_faces] piecewise constant pressure per face
+ *  hist          [n_nodes][3] Newmark history h_s; r_s = rho h_s (Sec. 4.2.3) */
+typedef struct {
+  const double* dir_values;
+  double pressure;
+  const double* node_pressure;
+  const double* face_pressure;
+  const double* hist;
+} fsi_load;
+
+/* Per-call statistics. */
+typedef struct {
+  int32_t newton_its;        /* Newton iterations performed */
+  int32_t krylov_its_total;  /* Krylov iterations summed over Newton iterations */
+  int32_t krylov_its_last;   /* Krylov iterations of the last linear solve */
+  int32_t status;            /* fsi_status of the call */
+  int32_t guess_accepted;    /* 1 if the supplied initial increment was kept */
+  int32_t n_levels;          /* AMG levels */
+  double res0;               /* ||R(v_0)||_2 */
+  double res;                /* ||R(v_k)||_2 at return */
+  double inc_norm;           /* ||v_k - v_(k-1)||_2 of the last update */
+  double lin_res;            /* relative residual of the last linear solve */
+} fsi_info;
+
+/* Default options: FP64, FGMRES(100), block Jacobi 3+3 sweeps, omega 0.7,
+ * Newton rtol 1e-8, Krylov rtol 1e-8, PSPG on, fibre_factor 2. */
+void fsi_solid_default_opts(fsi_solver_opts* opts);
+
+/* Build a handle: copies the mesh, computes the P1 geometry on the device,
+ * colours the elements (greedy first fit in element order), builds the 4x4
+ * block-CSR pattern, the element-to-block map and the AMG aggregation
+ * hierarchy.  Allocates all device memory the solver needs. */
+fsi_status fsi_solid_create(const fsi_mesh_desc* mesh, int32_t n_mat, const fsi_material* mats,
+                            const fsi_solver_opts* opts, fsi_solid_t* out);
+
+/* Release every resource of the handle.  NULL is accepted. */
+fsi_status fsi_solid_destroy(fsi_solid_t h);
+
+/* Residual R(v) of Eq. stabweakelas (R^1 rows 0..2, R^2 + W_s row 3 per node),
+ * minus the dead load, with zero rows on constrained components; and, when
+ * want_tangent != 0, the consistent Jacobian K = dR/dv (Eq. globsys) assembled
+ * into the library-owned BSR matrix with constrained rows/columns replaced by
+ * identity rows / zero columns.  state, residual: device FP64 [n_nodes][4].
+ * residual may be NULL when only the tangent is wanted. */
+fsi_status fsi_solid_residual_tangent(fsi_solid_t h, const double* state, const fsi_load* load,
+                                      double* residual, int32_t want_tangent, void* stream);
+
+/* The assembled level-0 matrix: 4x4 blocks, row-major within a block.
+ * row_ptr [n_nodes+1], col_idx [n_blocks] (device pointers owned by the
+ * library, valid until destroy); dtype 0 = FP64 values, 1 = FP32 values. */
+fsi_status fsi_solid_get_bsr(fsi_solid_t h, const int32_t** row_ptr, const int32_t** col_idx,
+                             const void** vals, int32_t* dtype, int32_t* n_blocks);
+
+/* y = K x with the assembled matrix (device FP64 [n_nodes][4] vectors). */
+fsi_status fsi_solid_spmv(fsi_solid_t h, const double* x, double* y, void* stream);
+
+/* Solve K x = b with the assembled matrix by the configured Krylov method and
+ * AMG preconditioner to krylov_rtol (b, x device FP64 [n_nodes][4]; x is
+ * used as the initial guess). */
+fsi_status fsi_solid_linear_solve(fsi_solid_t h, const double* b, double* x, fsi_info* info,
+                                  void* stream);
+
+/* One Newton iteration from `state` (Sec. 4.4 steps 1-2): residual, tangent,
+ * linear solve of K dv = -R, update state += dv.  info->res0 is ||R|| before. */
+fsi_status fsi_solid_newton_step(fsi_solid_t h, double* state, const fsi_load* load,
+                                 fsi_info* info, void* stream);
+
+/* Newton's method to newton_rtol for one load step.  Writes load->dir_values
+ * into the constrained components first.  guess (device [n_nodes][4] or NULL)
+ * is an initial increment: it is kept only if ||R(v + guess)|| <= ||R(v)||,
+ * else Newton starts from v (zero increment). */
+fsi_status fsi_solid_solve(fsi_solid_t h, double* state, const fsi_load* load, const double* guess,
+                           fsi_info* info, void* stream);
+
+/* Host copy of the element colouring in original element order
+ * (colour_out [n_elems]); returns the number of colours in *n_colours. */
+fsi_status fsi_solid_get_colouring(fsi_solid_t h, int32_t* colour_out, int32_t* n_colours);
+
+/* AMG level sizes: nodes_out[l] for l < *n_levels (host, capacity max_levels). */
+fsi_status fsi_solid_get_levels(fsi_solid_t h, int32_t* nodes_out, int32_t* blocks_out,
+                                int32_t capacity, int32_t* n_levels);
+
+/* Kernel classes of the launch accounting below. */
+enum {
+  FSI_KC_TANGENT = 0,  /* element residual + tangent + colour-ordered block scatter */
+  FSI_KC_RESIDUAL,     /* element residual only */
+  FSI_KC_JACOBI0,      /* damped block-Jacobi sweep on the finest level */
+  FSI_KC_BSR0,         /* other finest-level block-row kernels (SpMV, residual) */
+  FSI_KC_COARSE_BSR,   /* block-row kernels on coarser levels */
+  FSI_KC_TRANSFER,     /* restriction / prolongation */
+  FSI_KC_GALERKIN,     /* per-Newton-step numeric AMG set-up */
+  FSI_KC_BLOCKINV,     /* block-diagonal inverses */
+  FSI_KC_COARSE,       /* dense coarsest-level factorisation and solve */
+  FSI_KC_VECTOR,       /* Krylov vector kernels and reductions */
+  FSI_KC_OTHER,
+  FSI_KC_COUNT
+};
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t fsi_solid_launch_count(void);
+
+/* Per-class kernel timing of one handle.  Returns in ms_out[FSI_KC_COUNT] the
+ * device time (sum of CUDA-event intervals recorded on the launching stream
+ * around each launch) and in launches_out[FSI_KC_COUNT] the launch counts
+ * accumulated since the previous call, then resets them; enable = 1 keeps
+ * (or starts) recording for the following calls on this handle, enable = 0
+ * stops it.  Either output pointer may be NULL. */
+fsi_status fsi_solid_kernel_timing(fsi_solid_t h, int32_t enable, double* ms_out, int64_t* launches_out);
+
+/* Description of the last error on this handle (static storage of the handle). */
+const char* fsi_solid_last_error(fsi_solid_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSI_SOLID_H */

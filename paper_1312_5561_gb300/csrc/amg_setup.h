@@ -1,0 +1,51 @@
+// Host data structures of the smoothed-aggregation AMG set-up.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+namespace fsi {
+
+// Block-sparse matrix on the host: n block rows, nc block columns, blocks
+// br x bc stored row-major; column indices sorted within each row.
+struct HostBsr {
+  int n = 0, nc = 0, br = 0, bc = 0;
+  std::vector<int32_t> rp, ci;
+  std::vector<double> v;
+  int nb() const { return (int)ci.size(); }
+};
+
+struct HostLevel {
+  HostBsr A;                    // level operator at the reference state (level 0: reference tangent)
+  std::vector<uint8_t> free;    // [n * br] 1 = free unknown
+  std::vector<double> Dinv;     // [n][br][br] inverses of the diagonal blocks
+  std::vector<int32_t> comp;    // component (segment) of each node
+  // transfer to the next coarser level (absent on the coarsest level)
+  std::vector<int32_t> agg;     // aggregate of each node
+  std::vector<double> Pt;       // [n][br][7] tentative prolongator rows (one block per node)
+  double omega_p = 0.0;         // prolongator smoothing weight 4 / (3 lambda_max(D^-1 A))
+  HostBsr P, PT;                // smoothed prolongator and its transpose (reference values)
+  std::vector<int32_t> pt_src;  // PT block t holds the transpose of P block pt_src[t]
+  std::vector<int32_t> w_ptr, w_k;          // W = A Pt: A blocks summed into each P block
+  HostBsr AP;                               // A P pattern
+  std::vector<int32_t> ap_ptr, ap_pairs;    // A P: (A block, P block) pairs per AP block
+  std::vector<int32_t> ac_ptr, ac_pairs;    // P^T (A P): (P block, AP block) pairs per coarse block
+  std::vector<int32_t> fix_blk, fix_dof;    // coarse unknowns with no fine support: identity rows
+};
+
+struct HostCoarse {
+  std::vector<int32_t> comp_ptr;   // node ranges of the components of the coarsest level
+  std::vector<int64_t> inv_off;    // offsets of the dense inverses
+  std::vector<double> inv;         // dense inverses (unused when the device factorises)
+  int max_dofs = 0;
+};
+
+// Builds levels[0..] from the level-0 matrix A0 (4x4 blocks), its free mask,
+// the node coordinates X [n][3] and components comp0 (non-decreasing).
+void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
+                        const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap,
+                        std::vector<HostLevel>& levels, HostCoarse& coarse);
+
+}  // namespace fsi

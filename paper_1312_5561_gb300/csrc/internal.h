@@ -1,0 +1,244 @@
+// Internal declarations shared by the translation units of libfsi_solid.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fsi_solid.h"
+
+// ------------------------------------------------------------------ launch accounting
+// Every kernel launch of the library goes through FSI_LAUNCH, which counts it
+// and, while a handle's kernel timing is switched on, brackets it with a pair
+// of CUDA events recorded on the launching stream.
+namespace fsi {
+enum KernelClass {
+  KC_TANGENT = 0,     // element residual + tangent + colour-ordered scatter
+  KC_RESIDUAL,        // element residual only
+  KC_JACOBI0,         // damped block-Jacobi sweep (x + w D^-1 (b - A x)) on the finest level
+  KC_BSR0,            // other finest-level block-row kernels (SpMV, residual)
+  KC_COARSE_BSR,      // block-row kernels on coarser levels (smoothing, residuals)
+  KC_TRANSFER,        // restriction / prolongation
+  KC_GALERKIN,        // numeric set-up: smoothed P, P^T, A P, P^T A P
+  KC_BLOCKINV,        // block-diagonal inverses
+  KC_COARSE,          // dense coarsest-level factorisation and solve
+  KC_VECTOR,          // Krylov vector kernels and reductions
+  KC_OTHER,
+  KC_COUNT
+};
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> cls;      // class of pair p (events 2p, 2p+1)
+  size_t used = 0;
+};
+extern thread_local Profiler* g_prof;
+extern long long g_launches;
+void launch_begin(int cls, cudaStream_t s);
+void launch_end(cudaStream_t s);
+}  // namespace fsi
+
+#define FSI_LAUNCH(cls, s, ...)      \
+  do {                               \
+    fsi::launch_begin((cls), (s));   \
+    __VA_ARGS__;                     \
+    fsi::launch_end((s));            \
+  } while (0)
+
+
+namespace fsi {
+
+// ------------------------------------------------------------------ host setup
+struct HostPattern {
+  std::vector<int32_t> row_ptr;   // [n+1]
+  std::vector<int32_t> col_idx;   // [nb], sorted within a row
+};
+
+// Greedy first-fit colouring of elements in element order: an element takes
+// the smallest colour not used by an earlier element sharing a vertex.
+int colour_elements(int n_nodes, int n_elems, const int32_t* tets, std::vector<int32_t>& colour);
+
+// Node adjacency through shared elements (every node is its own neighbour).
+void element_pattern(int n_nodes, int n_elems, const int32_t* tets, HostPattern& pat);
+
+// Find block (i, j) in a pattern; -1 if absent.
+int32_t find_block(const HostPattern& pat, int32_t i, int32_t j);
+
+// Deterministic greedy aggregation of a node graph (see the definition in setup.cpp).
+// comp[i] = connected component (segment) of node i; aggregates never cross
+// components and are numbered component-major.  Returns the number of aggregates.
+int aggregate_nodes(const HostPattern& pat, const std::vector<int32_t>& comp, std::vector<int32_t>& agg);
+
+// Pattern of the Galerkin product P^T K P for a block-identity P over aggregates.
+void coarse_pattern(const HostPattern& fine, const std::vector<int32_t>& agg, int n_coarse,
+                    HostPattern& coarse);
+
+// ------------------------------------------------------------------ device level
+// One level of the AMG hierarchy.  Level 0 holds the assembled tangent (4x4
+// blocks); coarser levels hold Galerkin operators with 7x7 blocks.  P maps
+// the next coarser level to this one (blocks bs x 7), PT is its transpose.
+struct Level {
+  int n = 0;                 // block rows
+  int nb = 0;                // stored blocks
+  int bs = 4;                // block size of this level
+  int32_t* row_ptr = nullptr;
+  int32_t* col_idx = nullptr;
+  int32_t* diag_idx = nullptr;
+  int32_t* block_row = nullptr;
+  void* vals = nullptr;      // T [nb][bs*bs]
+  void* dinv = nullptr;      // T [n][bs*bs] inverses of the diagonal blocks
+  uint8_t* cmask = nullptr;  // level 0: [n][4] 1 = constrained component
+  // prolongation from level+1 (rows: this level's nodes) and restriction (its transpose)
+  int p_nb = 0, pt_nb = 0;
+  int32_t* p_rp = nullptr;
+  int32_t* p_ci = nullptr;
+  void* p_v = nullptr;       // T [p_nb][bs*7]
+  int32_t* pt_rp = nullptr;
+  int32_t* pt_ci = nullptr;
+  void* pt_v = nullptr;      // T [pt_nb][7*bs]
+  // numeric set-up of the next level (fixed plans, values recomputed per Newton step)
+  int32_t* agg = nullptr;        // [n] aggregate of each node
+  void* ptent = nullptr;         // T [n][bs*7] tentative prolongator rows
+  uint8_t* freem = nullptr;      // [n*bs] 1 = free unknown
+  double omega_p = 0.0;
+  int32_t* p_brow = nullptr;     // [p_nb] block row of each P block
+  int32_t* w_ptr = nullptr;      // [p_nb+1]
+  int32_t* w_k = nullptr;        // A blocks summed into each W = A P_t block
+  void* w_v = nullptr;           // T [p_nb][bs*7]
+  int32_t* pt_src = nullptr;     // [p_nb] P block transposed into PT block t
+  int ap_nb = 0;
+  int32_t* ap_ptr = nullptr;     // [ap_nb+1]
+  int32_t* ap_pairs = nullptr;   // (A block, P block) pairs
+  void* ap_v = nullptr;          // T [ap_nb][bs*7]
+  int32_t* ac_ptr = nullptr;     // [nb of next level + 1]
+  int32_t* ac_pairs = nullptr;   // (P block, AP block) pairs
+  int n_fix = 0;
+  int32_t* fix_blk = nullptr;    // identity rows of the next level
+  int32_t* fix_dof = nullptr;
+  // V-cycle vectors (T)
+  void* x = nullptr;
+  void* x2 = nullptr;
+  void* b = nullptr;
+  void* r = nullptr;
+  HostPattern hpat;          // level 0 pattern (host copy)
+};
+
+struct Coarse {              // block-diagonal dense inverse of the coarsest level
+  int n_comp = 0;
+  int max_dofs = 0;
+  bool on_device_factor = false;  // single-level hierarchies factorise K itself each Newton step
+  int32_t* comp_ptr = nullptr;   // [n_comp+1] node ranges (components are contiguous)
+  int64_t* inv_off = nullptr;    // [n_comp] offsets into inv (in entries)
+  void* inv = nullptr;           // T dense inverses, row-major per component
+  double* work = nullptr;        // FP64 factorisation workspace (same layout as inv)
+};
+
+struct Handle {
+  // sizes
+  int n_nodes = 0, n_elems = 0, n_faces = 0, n_mat = 0, n_colours = 0, n_seg = 1;
+  fsi_solver_opts opts{};
+  std::string last_error;
+  int precision = 0;   // 0 fp64, 1 fp32
+
+  // element data, colour-major order
+  std::vector<int32_t> colour_host;     // [n_elems] original order
+  std::vector<int32_t> colour_ptr;      // [n_colours+1] ranges in colour-major order
+  std::vector<int32_t> elem_perm_host;  // colour-major position -> original element
+  int32_t* d_conn = nullptr;     // [n_elems][4]
+  double* d_geo = nullptr;       // [n_elems][16]: g (12), V, tauV, 0, 0
+  double* d_fibre = nullptr;     // [n_elems][6]
+  int32_t* d_mat = nullptr;      // [n_elems]
+  int32_t* d_slot = nullptr;     // [n_elems][16] block index of (a, b)
+  double* d_mats = nullptr;      // [n_mat][8]: model, c10, c01, k1, k2, kappa, rho, mu_l
+  double* d_X = nullptr;         // [n_nodes][3]
+  uint8_t* d_dir_mask = nullptr; // [n_nodes][4]
+  int32_t* d_faces = nullptr;    // [n_faces][3]
+  int32_t* d_nf_ptr = nullptr;   // [n_nodes+1] node -> (face, local vertex) incidence
+  int32_t* d_nf_idx = nullptr;   // [3 n_faces]: 3 * face + local vertex
+  int32_t* d_seg_node = nullptr; // [n_nodes]
+  int* d_err = nullptr;          // device error word (bit 0 inverted, bit 1 bounds)
+
+  // AMG hierarchy (level 0 = assembled matrix)
+  std::vector<Level> levels;
+  Coarse coarse;
+
+  // Krylov workspace (FP64)
+  int m = 30;
+  double* d_V = nullptr;     // [(m+1)][ndof]
+  double* d_Z = nullptr;     // [m][ndof]
+  double* d_w = nullptr;     // [ndof]
+  double* d_r = nullptr;     // [ndof]
+  double* d_t = nullptr;     // [ndof] scratch
+  double* d_t2 = nullptr;    // [ndof] scratch
+  double* d_t3 = nullptr;    // [ndof] scratch
+  double* d_partial = nullptr;   // reduction partials [n_red_blocks * 72]
+  double* d_dots = nullptr;      // [72]
+  double* h_dots = nullptr;      // pinned host [72]
+  float* d_xs = nullptr;         // FP32 vector scratch for the mixed precision preconditioner
+  float* d_ys = nullptr;
+  double* d_fext = nullptr;      // [n_nodes][3]
+  double* d_state_tmp = nullptr; // [ndof]
+  double* d_res = nullptr;       // [ndof]
+  int red_blocks = 0;
+
+  cudaStream_t stream = nullptr;
+  struct Profiler* prof_ptr() { return &prof; }
+  Profiler prof;
+};
+
+// ------------------------------------------------------------------ kernels (launchers)
+// element.cu
+void launch_geometry(Handle& h, cudaStream_t s);
+void launch_external_force(Handle& h, const fsi_load* load, cudaStream_t s);
+// Residual (if residual != nullptr) and tangent (if want_tangent) at `state`;
+// the tangent goes to level 0 (or to vals_target, FP32 if target_fp32 == 1).
+void launch_assemble(Handle& h, const double* state, const double* hist, double* residual,
+                     bool want_tangent, cudaStream_t s, void* vals_target = nullptr, int target_fp32 = -1);
+void launch_set_dirichlet_values(Handle& h, double* state, const double* values, cudaStream_t s);
+
+// linalg.cu
+template <typename T>
+void launch_spmv(const Level& L, const T* x, T* y, cudaStream_t s);
+void launch_spmv_f64acc(const Level& L, const double* x, double* y, bool fp32vals, cudaStream_t s);
+void launch_residual_f64(const Level& L, const double* b, const double* x, double* r, bool fp32vals,
+                         cudaStream_t s);
+void launch_block_inverse(Level& L, bool fp32, int* err, cudaStream_t s);
+// numeric set-up of level+1 from level (smoothed P, P^T, A P, P^T A P)
+void launch_galerkin(Level& L, Level& C, bool fp32, cudaStream_t s);
+void launch_coarse_factor(Handle& h, bool fp32, cudaStream_t s);
+template <typename T>
+void vcycle(Handle& h, int level, cudaStream_t s);
+// FP64 vector helpers; reductions are deterministic (fixed two-pass order)
+// out_dev[i] = V_i . y for V_i = V + i ldv, i < k
+void dots(Handle& h, const double* V, long ldv, int k, const double* y, long n, double* out_dev,
+          cudaStream_t s);
+void multi_axpy(const double* coef_dev, const double* V, int k, long n, double* w, double sign,
+                cudaStream_t s);
+void axpy(double a, const double* x, double* y, long n, cudaStream_t s);
+void scale_copy(double a, const double* x, double* y, long n, cudaStream_t s);
+void to_float(const double* x, float* y, long n, cudaStream_t s);
+void to_double(const float* x, double* y, long n, cudaStream_t s);
+void mask_vector(const uint8_t* cmask, double* x, long n, cudaStream_t s);
+
+}  // namespace fsi
+
+#define FSI_CUDA_TRY(expr)                                                         \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      throw fsi::CudaError(std::string(#expr) + ": " + cudaGetErrorString(_e));     \
+    }                                                                              \
+  } while (0)
+
+namespace fsi {
+struct CudaError {
+  std::string msg;
+  explicit CudaError(std::string m) : msg(std::move(m)) {}
+};
+struct ArgError {
+  std::string msg;
+  explicit ArgError(std::string m) : msg(std::move(m)) {}
+};
+}  // namespace fsi

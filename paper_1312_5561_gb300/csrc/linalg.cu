@@ -1,0 +1,647 @@
+// Sparse and dense linear algebra of the linear solve: 4x4 block-CSR SpMV and
+// residuals, damped block-Jacobi smoothing, aggregation transfers, Galerkin
+// coarse operators, the block-diagonal dense coarse solve and the FP64
+// vector kernels of the Krylov method (deterministic reductions).
+#include <cmath>
+#include <utility>
+
+#include "internal.h"
+
+namespace fsi {
+
+namespace {
+
+inline int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<double> {
+  __device__ __forceinline__ static void load(const double* p, double v[4]) {
+    double2 a = reinterpret_cast<const double2*>(p)[0];
+    double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ __forceinline__ static void store(double* p, const double v[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+template <>
+struct Vec4<float> {
+  __device__ __forceinline__ static void load(const float* p, float v[4]) {
+    float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  __device__ __forceinline__ static void store(float* p, const float v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+template <int R>
+struct Lanes {
+  static constexpr int v = R <= 4 ? 4 : 8;
+};
+
+// Block-row kernel for R x C blocks: a group of Lanes<R> threads owns one
+// block row; thread r accumulates row r of every block of that row.
+//   MODE 0: y = A x     MODE 1: y = b - A x     MODE 3: y += A x
+//   MODE 2: y = x + omega D^-1 (b - A x)   (one damped block-Jacobi sweep, R == C)
+template <typename TV, typename TX, typename TA, int R, int C, int MODE>
+__global__ void bsr_kernel(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                           const TV* __restrict__ vals, const TX* __restrict__ x, const TX* __restrict__ b,
+                           const TV* __restrict__ dinv, TA omega, TX* __restrict__ y) {
+  constexpr int LN = Lanes<R>::v;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t / LN, r = t % LN;
+  const bool active = row < n && r < R;
+  TA acc = 0;
+  if (active) {
+    const int k0 = row_ptr[row], k1 = row_ptr[row + 1];
+    for (int k = k0; k < k1; ++k) {
+      const int j = col_idx[k];
+      const TV* a = vals + (size_t)k * (R * C) + r * C;
+      const TX* xv = x + (size_t)j * C;
+      if constexpr (C == 4) {
+        TV v[4];
+        TX xx[4];
+        Vec4<TV>::load(a, v);
+        Vec4<TX>::load(xv, xx);
+        acc += (TA)v[0] * (TA)xx[0] + (TA)v[1] * (TA)xx[1] + (TA)v[2] * (TA)xx[2] + (TA)v[3] * (TA)xx[3];
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc += (TA)a[c] * (TA)xv[c];
+      }
+    }
+  }
+  const size_t o = (size_t)row * R + r;
+  if constexpr (MODE == 0) {
+    if (active) y[o] = (TX)acc;
+  } else if constexpr (MODE == 1) {
+    if (active) y[o] = (TX)((TA)b[o] - acc);
+  } else if constexpr (MODE == 3) {
+    if (active) y[o] = (TX)((TA)y[o] + acc);
+  } else {
+    static_assert(R == C, "Jacobi sweep needs square blocks");
+    const TA res = active ? (TA)b[o] - acc : (TA)0;
+    const unsigned base = (threadIdx.x & 31) & ~(unsigned)(LN - 1);
+    TA rr[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) rr[c] = __shfl_sync(0xffffffffu, res, base + c);
+    if (active) {
+      const TV* d = dinv + (size_t)row * (R * R) + r * R;
+      TA corr = 0;
+#pragma unroll
+      for (int c = 0; c < R; ++c) corr += (TA)d[c] * rr[c];
+      y[o] = (TX)((TA)x[o] + omega * corr);
+    }
+  }
+}
+
+// x = omega D^-1 b (first Jacobi sweep from a zero guess), B x B blocks
+template <typename T, int B>
+__global__ void jacobi_zero_kernel(int n, const T* __restrict__ dinv, const T* __restrict__ b, T omega,
+                                   T* __restrict__ x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t / B, r = t % B;
+  if (row >= n) return;
+  const T* d = dinv + (size_t)row * (B * B) + r * B;
+  const T* bv = b + (size_t)row * B;
+  T acc = 0;
+#pragma unroll
+  for (int c = 0; c < B; ++c) acc += d[c] * bv[c];
+  x[(size_t)row * B + r] = omega * acc;
+}
+
+// Inverse of each B x B diagonal block (Gauss-Jordan, partial pivoting, FP64).
+template <typename T, int B>
+__global__ void block_inverse_kernel(int n, const int32_t* __restrict__ diag_idx, const T* __restrict__ vals,
+                                     T* __restrict__ dinv, int* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[B][2 * B];
+  const T* v = vals + (size_t)(B * B) * diag_idx[i];
+  for (int r = 0; r < B; ++r)
+    for (int c = 0; c < B; ++c) {
+      a[r][c] = (double)v[B * r + c];
+      a[r][B + c] = (r == c) ? 1.0 : 0.0;
+    }
+  bool ok = true;
+  for (int k = 0; k < B; ++k) {
+    int p = k;
+    double best = fabs(a[k][k]);
+    for (int r = k + 1; r < B; ++r)
+      if (fabs(a[r][k]) > best) { best = fabs(a[r][k]); p = r; }
+    if (!(best > 0.0)) { ok = false; break; }
+    if (p != k)
+      for (int c = 0; c < 2 * B; ++c) { double t = a[k][c]; a[k][c] = a[p][c]; a[p][c] = t; }
+    const double ip = 1.0 / a[k][k];
+    for (int c = 0; c < 2 * B; ++c) a[k][c] *= ip;
+    for (int r = 0; r < B; ++r) {
+      if (r == k) continue;
+      const double f = a[r][k];
+      for (int c = 0; c < 2 * B; ++c) a[r][c] -= f * a[k][c];
+    }
+  }
+  T* o = dinv + (size_t)(B * B) * i;
+  for (int r = 0; r < B; ++r)
+    for (int c = 0; c < B; ++c) o[B * r + c] = ok ? (T)a[r][B + c] : T(0);
+  if (!ok) atomicOr(err, 4);
+}
+
+constexpr int NS = 7;
+
+// W[q] = sum over the plan of A_k P_t(col(k))   (B x B times B x 7)
+template <typename T, int B>
+__global__ void galerkin_w_kernel(int p_nb, const int32_t* __restrict__ w_ptr, const int32_t* __restrict__ w_k,
+                                  const int32_t* __restrict__ a_ci, const T* __restrict__ a_v,
+                                  const T* __restrict__ ptent, T* __restrict__ w_v) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (int)(t / (B * NS)), e = (int)(t % (B * NS));
+  if (q >= p_nb) return;
+  const int r = e / NS, c = e % NS;
+  T acc = 0;
+  for (int s = w_ptr[q]; s < w_ptr[q + 1]; ++s) {
+    const int k = w_k[s];
+    const T* a = a_v + (size_t)k * (B * B) + r * B;
+    const T* p = ptent + (size_t)a_ci[k] * (B * NS) + c;
+#pragma unroll
+    for (int m = 0; m < B; ++m) acc += a[m] * p[m * NS];
+  }
+  w_v[(size_t)q * (B * NS) + e] = acc;
+}
+
+// P[q] = free (.) ([col(q) == agg(i)] P_t(i) - omega D_i^-1 W[q])
+template <typename T, int B>
+__global__ void galerkin_p_kernel(int p_nb, const int32_t* __restrict__ p_brow, const int32_t* __restrict__ p_ci,
+                                  const int32_t* __restrict__ agg, const uint8_t* __restrict__ freem,
+                                  const T* __restrict__ dinv, const T* __restrict__ ptent, const T* __restrict__ w_v,
+                                  T omega, T* __restrict__ p_v) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (int)(t / (B * NS)), e = (int)(t % (B * NS));
+  if (q >= p_nb) return;
+  const int r = e / NS, c = e % NS;
+  const int i = p_brow[q];
+  T v = 0;
+  if (freem[(size_t)i * B + r]) {
+    const T* d = dinv + (size_t)i * (B * B) + r * B;
+    const T* w = w_v + (size_t)q * (B * NS) + c;
+    T acc = 0;
+#pragma unroll
+    for (int m = 0; m < B; ++m) acc += d[m] * w[m * NS];
+    v = -omega * acc;
+    if (p_ci[q] == agg[i]) v += ptent[(size_t)i * (B * NS) + e];
+  }
+  p_v[(size_t)q * (B * NS) + e] = v;
+}
+
+// PT[t] = P[pt_src[t]]^T  (7 x B blocks)
+template <typename T, int B>
+__global__ void galerkin_pt_kernel(int p_nb, const int32_t* __restrict__ pt_src, const T* __restrict__ p_v,
+                                   T* __restrict__ pt_v) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int u = (int)(t / (B * NS)), e = (int)(t % (B * NS));
+  if (u >= p_nb) return;
+  const int r = e / B, c = e % B;   // PT block entry (r, c) = P entry (c, r)
+  pt_v[(size_t)u * (B * NS) + e] = p_v[(size_t)pt_src[u] * (B * NS) + c * NS + r];
+}
+
+// AP[r] = sum over the plan of A_k P_q   (B x B times B x 7)
+template <typename T, int B>
+__global__ void galerkin_ap_kernel(int ap_nb, const int32_t* __restrict__ ap_ptr, const int32_t* __restrict__ pairs,
+                                   const T* __restrict__ a_v, const T* __restrict__ p_v, T* __restrict__ ap_v) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = (int)(t / (B * NS)), e = (int)(t % (B * NS));
+  if (o >= ap_nb) return;
+  const int r = e / NS, c = e % NS;
+  T acc = 0;
+  for (int s = ap_ptr[o]; s < ap_ptr[o + 1]; ++s) {
+    const T* a = a_v + (size_t)pairs[2 * s] * (B * B) + r * B;
+    const T* p = p_v + (size_t)pairs[2 * s + 1] * (B * NS) + c;
+#pragma unroll
+    for (int m = 0; m < B; ++m) acc += a[m] * p[m * NS];
+  }
+  ap_v[(size_t)o * (B * NS) + e] = acc;
+}
+
+// Ac[o] = sum over the plan of P_q^T AP_r   (7 x B times B x 7)
+template <typename T, int B>
+__global__ void galerkin_ac_kernel(int ac_nb, const int32_t* __restrict__ ac_ptr, const int32_t* __restrict__ pairs,
+                                   const T* __restrict__ p_v, const T* __restrict__ ap_v, T* __restrict__ c_v) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = (int)(t / (NS * NS)), e = (int)(t % (NS * NS));
+  if (o >= ac_nb) return;
+  const int r = e / NS, c = e % NS;
+  T acc = 0;
+  for (int s = ac_ptr[o]; s < ac_ptr[o + 1]; ++s) {
+    const T* p = p_v + (size_t)pairs[2 * s] * (B * NS) + r;
+    const T* ap = ap_v + (size_t)pairs[2 * s + 1] * (B * NS) + c;
+#pragma unroll
+    for (int m = 0; m < B; ++m) acc += p[m * NS] * ap[m * NS];
+  }
+  c_v[(size_t)o * (NS * NS) + e] = acc;
+}
+
+template <typename T>
+__global__ void identity_fix_kernel(int n_fix, const int32_t* __restrict__ blk, const int32_t* __restrict__ dof,
+                                    T* __restrict__ vals) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_fix) return;
+  vals[(size_t)blk[t] * (NS * NS) + dof[t] * (NS + 1)] = T(1);
+}
+
+// In-place Gauss-Jordan inversion (partial pivoting) of the dense operator of
+// each coarse component; one CTA per component, FP64 working storage.
+template <typename T>
+__global__ void coarse_factor_kernel(int bs, const int32_t* __restrict__ comp_ptr, const int64_t* __restrict__ inv_off,
+                                     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                                     const T* __restrict__ vals, double* __restrict__ work, T* __restrict__ inv,
+                                     int* __restrict__ err) {
+  const int comp = blockIdx.x;
+  const int n0 = comp_ptr[comp], n1 = comp_ptr[comp + 1];
+  const int nd = bs * (n1 - n0);
+  double* A = work + inv_off[comp];
+  __shared__ int piv_row;
+  __shared__ double s_best[32];
+  __shared__ int s_idx[32];
+  extern __shared__ int s_perm[];
+  for (long k = threadIdx.x; k < (long)nd * nd; k += blockDim.x) A[k] = 0.0;
+  __syncthreads();
+  for (int i = n0 + threadIdx.x; i < n1; i += blockDim.x) {
+    for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      const int j = col_idx[k];
+      if (j < n0 || j >= n1) continue;
+      for (int r = 0; r < bs; ++r)
+        for (int c = 0; c < bs; ++c)
+          A[(size_t)(bs * (i - n0) + r) * nd + bs * (j - n0) + c] = (double)vals[(size_t)(bs * bs) * k + bs * r + c];
+    }
+  }
+  __syncthreads();
+  bool singular = false;
+  for (int k = 0; k < nd; ++k) {
+    // pivot search in column k, rows k..nd-1
+    double best = -1.0;
+    int bi = k;
+    for (int r = k + threadIdx.x; r < nd; r += blockDim.x) {
+      double v = fabs(A[(size_t)r * nd + k]);
+      if (v > best) { best = v; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { s_best[threadIdx.x >> 5] = best; s_idx[threadIdx.x >> 5] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = -1.0;
+      int idx = k;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        if (s_best[w] > b || (s_best[w] == b && s_idx[w] < idx)) { b = s_best[w]; idx = s_idx[w]; }
+      piv_row = (b > 0.0) ? idx : -1;
+      s_perm[k] = idx;
+    }
+    __syncthreads();
+    const int p = piv_row;
+    if (p < 0) { singular = true; break; }
+    if (p != k)
+      for (int c = threadIdx.x; c < nd; c += blockDim.x) {
+        double t = A[(size_t)k * nd + c];
+        A[(size_t)k * nd + c] = A[(size_t)p * nd + c];
+        A[(size_t)p * nd + c] = t;
+      }
+    __syncthreads();
+    const double ip = 1.0 / A[(size_t)k * nd + k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < nd; c += blockDim.x) {
+      double v = (c == k) ? 1.0 : A[(size_t)k * nd + c];
+      A[(size_t)k * nd + c] = v * ip;
+    }
+    __syncthreads();
+    for (long q = threadIdx.x; q < (long)nd * nd; q += blockDim.x) {
+      const int r = (int)(q / nd), c = (int)(q % nd);
+      if (r == k) continue;
+      const double f = A[(size_t)r * nd + k];
+      if (c == k) continue;
+      A[(size_t)r * nd + c] -= f * A[(size_t)k * nd + c];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nd; r += blockDim.x) {
+      if (r == k) continue;
+      A[(size_t)r * nd + k] = -A[(size_t)r * nd + k] * A[(size_t)k * nd + k];
+    }
+    __syncthreads();
+  }
+  if (singular) {
+    if (threadIdx.x == 0) atomicOr(err, 8);
+    return;
+  }
+  // undo the row interchanges as column interchanges, in reverse order
+  for (int k = nd - 1; k >= 0; --k) {
+    const int p = s_perm[k];
+    if (p != k)
+      for (int r = threadIdx.x; r < nd; r += blockDim.x) {
+        double t = A[(size_t)r * nd + k];
+        A[(size_t)r * nd + k] = A[(size_t)r * nd + p];
+        A[(size_t)r * nd + p] = t;
+      }
+    __syncthreads();
+  }
+  T* o = inv + inv_off[comp];
+  for (long q = threadIdx.x; q < (long)nd * nd; q += blockDim.x) o[q] = (T)A[q];
+}
+
+// x_comp = Inv_comp b_comp
+template <typename T>
+__global__ void coarse_apply_kernel(int bs, const int32_t* __restrict__ comp_ptr, const int64_t* __restrict__ inv_off,
+                                    const T* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
+  const int comp = blockIdx.x;
+  const int n0 = comp_ptr[comp], n1 = comp_ptr[comp + 1];
+  const int nd = bs * (n1 - n0);
+  const T* A = inv + inv_off[comp];
+  const T* bb = b + (size_t)bs * n0;
+  for (int r = threadIdx.x; r < nd; r += blockDim.x) {
+    T acc = 0;
+    for (int c = 0; c < nd; ++c) acc += A[(size_t)r * nd + c] * bb[c];
+    x[(size_t)bs * n0 + r] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- FP64 vector kernels
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double s[kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < kRedThreads / 32) ? s[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+
+// partial[i * nblk + blk] = sum over this block's chunk of V_i . y   (V_i = V + i ldv)
+__global__ void multidot_kernel(const double* __restrict__ V, long ldv, const double* __restrict__ y, long n,
+                                double* __restrict__ partial) {
+  const int i = blockIdx.y;
+  const double* x = V + (size_t)i * ldv;
+  double acc = 0.0;
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+    acc += x[k] * y[k];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) acc += partial[(size_t)i * nblk + k];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[i] = acc;
+}
+
+// w += sign * sum_i coef[i] V_i   (V row-major [k][n]); coef in device memory
+__global__ void multi_axpy_kernel(const double* __restrict__ coef, const double* __restrict__ V, int k, long n,
+                                  double sign, double* __restrict__ w) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += coef[i] * V[(size_t)i * n + t];
+    w[t] += sign * acc;
+  }
+}
+
+__global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    y[t] += a * x[t];
+}
+
+__global__ void scale_copy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    y[t] = a * x[t];
+}
+
+__global__ void to_float_kernel(const double* __restrict__ x, float* __restrict__ y, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    y[t] = (float)x[t];
+}
+
+__global__ void to_double_kernel(const float* __restrict__ x, double* __restrict__ y, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    y[t] = (double)x[t];
+}
+
+__global__ void mask_vector_kernel(const uint8_t* __restrict__ cmask, double* __restrict__ x, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    if (cmask[t]) x[t] = 0.0;
+}
+
+inline int grid_stride_blocks(long n) {
+  long b = (n + 255) / 256;
+  return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+template <typename TV, typename TX, typename TA, int R, int C, int MODE>
+static void bsr_launch(int n, const int32_t* rp, const int32_t* ci, const void* vals, const TX* x, const TX* b,
+                       const void* dinv, TA omega, TX* y, cudaStream_t s, int cls) {
+  constexpr int LN = Lanes<R>::v;
+  const long threads = (long)n * LN;
+  if (threads == 0) return;
+  FSI_LAUNCH(cls, s, bsr_kernel<TV, TX, TA, R, C, MODE><<<blocks_for(threads, 128), 128, 0, s>>>(
+      n, rp, ci, (const TV*)vals, x, b, (const TV*)dinv, omega, y));
+}
+
+template <typename T>
+void launch_spmv(const Level& L, const T* x, T* y, cudaStream_t s) {
+  if (L.bs == 4)
+    bsr_launch<T, T, T, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, T(0), y, s, fsi::KC_BSR0);
+  else
+    bsr_launch<T, T, T, 7, 7, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, T(0), y, s, fsi::KC_COARSE_BSR);
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+template void launch_spmv<double>(const Level&, const double*, double*, cudaStream_t);
+template void launch_spmv<float>(const Level&, const float*, float*, cudaStream_t);
+
+void launch_spmv_f64acc(const Level& L, const double* x, double* y, bool fp32vals, cudaStream_t s) {
+  if (fp32vals)
+    bsr_launch<float, double, double, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, 0.0, y, s, fsi::KC_BSR0);
+  else
+    bsr_launch<double, double, double, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, 0.0, y, s, fsi::KC_BSR0);
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_residual_f64(const Level& L, const double* b, const double* x, double* r, bool fp32vals,
+                         cudaStream_t s) {
+  if (fp32vals)
+    bsr_launch<float, double, double, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, x, b, nullptr, 0.0, r, s, fsi::KC_BSR0);
+  else
+    bsr_launch<double, double, double, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, x, b, nullptr, 0.0, r, s, fsi::KC_BSR0);
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+template <typename T>
+static void block_inverse_t(Level& L, int* err, cudaStream_t s) {
+  if (L.bs == 4)
+    FSI_LAUNCH(fsi::KC_BLOCKINV, s, block_inverse_kernel<T, 4><<<blocks_for(L.n, 128), 128, 0, s>>>(L.n, L.diag_idx, (const T*)L.vals, (T*)L.dinv,
+                                                                    err));
+  else
+    FSI_LAUNCH(fsi::KC_BLOCKINV, s, block_inverse_kernel<T, 7><<<blocks_for(L.n, 64), 64, 0, s>>>(L.n, L.diag_idx, (const T*)L.vals, (T*)L.dinv,
+                                                                  err));
+}
+
+void launch_block_inverse(Level& L, bool fp32, int* err, cudaStream_t s) {
+  if (fp32)
+    block_inverse_t<float>(L, err, s);
+  else
+    block_inverse_t<double>(L, err, s);
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+template <typename T, int B>
+static void galerkin_t(Level& L, Level& C, cudaStream_t s) {
+  const long pe = (long)L.p_nb * B * NS;
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_w_kernel<T, B><<<blocks_for(pe, 256), 256, 0, s>>>(L.p_nb, L.w_ptr, L.w_k, L.col_idx, (const T*)L.vals,
+                                                              (const T*)L.ptent, (T*)L.w_v));
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_p_kernel<T, B><<<blocks_for(pe, 256), 256, 0, s>>>(L.p_nb, L.p_brow, L.p_ci, L.agg, L.freem,
+                                                              (const T*)L.dinv, (const T*)L.ptent, (const T*)L.w_v,
+                                                              (T)L.omega_p, (T*)L.p_v));
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_pt_kernel<T, B><<<blocks_for(pe, 256), 256, 0, s>>>(L.p_nb, L.pt_src, (const T*)L.p_v, (T*)L.pt_v));
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_kernel<T, B><<<blocks_for((long)L.ap_nb * B * NS, 256), 256, 0, s>>>(
+      L.ap_nb, L.ap_ptr, L.ap_pairs, (const T*)L.vals, (const T*)L.p_v, (T*)L.ap_v));
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ac_kernel<T, B><<<blocks_for((long)C.nb * NS * NS, 256), 256, 0, s>>>(
+      C.nb, L.ac_ptr, L.ac_pairs, (const T*)L.p_v, (const T*)L.ap_v, (T*)C.vals));
+  if (L.n_fix > 0)
+    FSI_LAUNCH(fsi::KC_GALERKIN, s, identity_fix_kernel<T><<<blocks_for(L.n_fix, 128), 128, 0, s>>>(L.n_fix, L.fix_blk, L.fix_dof, (T*)C.vals));
+}
+
+void launch_galerkin(Level& L, Level& C, bool fp32, cudaStream_t s) {
+  if (fp32) {
+    if (L.bs == 4) galerkin_t<float, 4>(L, C, s); else galerkin_t<float, 7>(L, C, s);
+  } else {
+    if (L.bs == 4) galerkin_t<double, 4>(L, C, s); else galerkin_t<double, 7>(L, C, s);
+  }
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_coarse_factor(Handle& h, bool fp32, cudaStream_t s) {
+  const Level& L = h.levels.back();
+  const Coarse& C = h.coarse;
+  size_t shm = sizeof(int) * (size_t)C.max_dofs;
+  if (fp32)
+    FSI_LAUNCH(fsi::KC_COARSE, s, coarse_factor_kernel<float><<<C.n_comp, 256, shm, s>>>(L.bs, C.comp_ptr, C.inv_off, L.row_ptr, L.col_idx,
+                                                           (const float*)L.vals, C.work, (float*)C.inv, h.d_err));
+  else
+    FSI_LAUNCH(fsi::KC_COARSE, s, coarse_factor_kernel<double><<<C.n_comp, 256, shm, s>>>(L.bs, C.comp_ptr, C.inv_off, L.row_ptr, L.col_idx,
+                                                            (const double*)L.vals, C.work, (double*)C.inv, h.d_err));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+template <typename T, int B>
+static void smooth_b(const Level& L, T omega, int sweeps, bool zero_start, cudaStream_t s) {
+  T* x = (T*)L.x;
+  T* x2 = (T*)L.x2;
+  const T* b = (const T*)L.b;
+  int k = 0;
+  if (zero_start) {
+    if (sweeps > 0) {
+      FSI_LAUNCH((B == 4 ? fsi::KC_BSR0 : fsi::KC_COARSE_BSR), s, jacobi_zero_kernel<T, B><<<blocks_for((long)L.n * B, 128), 128, 0, s>>>(L.n, (const T*)L.dinv, b, omega, x));
+      k = 1;
+    } else {
+      FSI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * B * (size_t)L.n, s));
+    }
+  }
+  for (; k < sweeps; ++k) {
+    bsr_launch<T, T, T, B, B, 2>(L.n, L.row_ptr, L.col_idx, L.vals, x, b, L.dinv, omega, x2, s, (B == 4 ? fsi::KC_JACOBI0 : fsi::KC_COARSE_BSR));
+    std::swap(x, x2);
+  }
+  // the result must live in L.x
+  if (x != (T*)L.x) FSI_CUDA_TRY(cudaMemcpyAsync(L.x, x, sizeof(T) * B * (size_t)L.n, cudaMemcpyDeviceToDevice, s));
+}
+
+template <typename T>
+static void smooth(const Level& L, T omega, int sweeps, bool zero_start, cudaStream_t s) {
+  if (L.bs == 4)
+    smooth_b<T, 4>(L, omega, sweeps, zero_start, s);
+  else
+    smooth_b<T, 7>(L, omega, sweeps, zero_start, s);
+}
+
+// One V-cycle on levels[level..]: approximately solves K_l x_l = b_l from x_l = 0.
+template <typename T>
+void vcycle(Handle& h, int level, cudaStream_t s) {
+  Level& L = h.levels[level];
+  const int nl = (int)h.levels.size();
+  const T omega = (T)h.opts.omega;
+  if (level == nl - 1) {
+    const Coarse& C = h.coarse;
+    FSI_LAUNCH(fsi::KC_COARSE, s, coarse_apply_kernel<T><<<C.n_comp, 256, 0, s>>>(L.bs, C.comp_ptr, C.inv_off, (const T*)C.inv, (const T*)L.b,
+                                                    (T*)L.x));
+    FSI_CUDA_TRY(cudaGetLastError());
+    return;
+  }
+  Level& Lc = h.levels[level + 1];
+  smooth<T>(L, omega, h.opts.nu_pre, true, s);
+  if (L.bs == 4) {
+    bsr_launch<T, T, T, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
+                                 (T*)L.r, s, fsi::KC_BSR0);
+    bsr_launch<T, T, T, 7, 4, 0>(Lc.n, L.pt_rp, L.pt_ci, L.pt_v, (const T*)L.r, nullptr, nullptr, T(0), (T*)Lc.b, s, fsi::KC_TRANSFER);
+  } else {
+    bsr_launch<T, T, T, 7, 7, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
+                                 (T*)L.r, s, fsi::KC_COARSE_BSR);
+    bsr_launch<T, T, T, 7, 7, 0>(Lc.n, L.pt_rp, L.pt_ci, L.pt_v, (const T*)L.r, nullptr, nullptr, T(0), (T*)Lc.b, s, fsi::KC_TRANSFER);
+  }
+  vcycle<T>(h, level + 1, s);
+  if (L.bs == 4)
+    bsr_launch<T, T, T, 4, 7, 3>(L.n, L.p_rp, L.p_ci, L.p_v, (const T*)Lc.x, nullptr, nullptr, T(0), (T*)L.x, s, fsi::KC_TRANSFER);
+  else
+    bsr_launch<T, T, T, 7, 7, 3>(L.n, L.p_rp, L.p_ci, L.p_v, (const T*)Lc.x, nullptr, nullptr, T(0), (T*)L.x, s, fsi::KC_TRANSFER);
+  smooth<T>(L, omega, h.opts.nu_post, false, s);
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+template void vcycle<double>(Handle&, int, cudaStream_t);
+template void vcycle<float>(Handle&, int, cudaStream_t);
+
+void dots(Handle& h, const double* V, long ldv, int k, const double* y, long n, double* out_dev, cudaStream_t s) {
+  dim3 grid(h.red_blocks, k);
+  FSI_LAUNCH(fsi::KC_VECTOR, s, multidot_kernel<<<grid, kRedThreads, 0, s>>>(V, ldv, y, n, h.d_partial));
+  FSI_LAUNCH(fsi::KC_VECTOR, s, reduce_partials_kernel<<<k, kRedThreads, 0, s>>>(h.d_partial, h.red_blocks, out_dev));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void multi_axpy(const double* coef_dev, const double* V, int k, long n, double* w, double sign, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, multi_axpy_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(coef_dev, V, k, n, sign, w));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void axpy(double a, const double* x, double* y, long n, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, axpy_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(a, x, y, n));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void scale_copy(double a, const double* x, double* y, long n, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, scale_copy_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(a, x, y, n));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void to_float(const double* x, float* y, long n, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, to_float_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, y, n));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void to_double(const float* x, double* y, long n, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, to_double_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, y, n));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void mask_vector(const uint8_t* cmask, double* x, long n, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, mask_vector_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(cmask, x, n));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+}  // namespace fsi

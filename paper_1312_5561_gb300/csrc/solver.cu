@@ -1,0 +1,873 @@
+// Handle set-up, AMG hierarchy, Krylov methods, Newton's method and the C ABI.
+//
+// Newton's method follows Sec. 4.4: at each iterate the residual R(v_k) of the
+// stabilised weak form (Eq. stabweakelas) and the consistent tangent K_k
+// (Eq. globsys) are assembled, K_k dv = -R(v_k) is solved by a Krylov method
+// to a relative reduction eps_1, and v_(k+1) = v_k + dv.  The stop test is
+// the relative residual ||R(v_k)|| <= eps_2 ||R(v_0)||; with adaptive_tol the
+// inner reduction follows eps_(1,k) = eps_(2,k-1)^2 (Sec. 4.4, end).
+//
+// The Krylov method is FGMRES(m) with classical Gram-Schmidt applied twice,
+// right-preconditioned by one V-cycle of an aggregation AMG on the 4x4 block
+// system (damped block-Jacobi smoothing, Galerkin coarse operators, a dense
+// block-diagonal solve on the coarsest level).  Vectors, orthogonalisation
+// and the outer residual are FP64; in FSI_PREC_FP32_IR the tangent and the
+// V-cycle are FP32 while the Newton residual stays FP64, so each Newton step
+// acts as one step of iterative refinement.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "amg_setup.h"
+#include "internal.h"
+
+namespace fsi {
+
+thread_local Profiler* g_prof = nullptr;
+long long g_launches = 0;
+static long long g_class_launches[KC_COUNT] = {0};
+
+void launch_begin(int cls, cudaStream_t s) {
+  ++g_launches;
+  if (cls >= 0 && cls < KC_COUNT) ++g_class_launches[cls];
+  Profiler* p = g_prof;
+  if (!p || !p->on) return;
+  if (p->pool.size() < 2 * (p->used + 1)) {
+    for (int q = 0; q < 2; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      p->pool.push_back(e);
+    }
+    p->cls.push_back(cls);
+  }
+  p->cls[p->used] = cls;
+  cudaEventRecord(p->pool[2 * p->used], s);
+}
+
+void launch_end(cudaStream_t s) {
+  Profiler* p = g_prof;
+  if (!p || !p->on || p->pool.size() < 2 * (p->used + 1)) return;
+  cudaEventRecord(p->pool[2 * p->used + 1], s);
+  ++p->used;
+}
+
+// Sets the handle's profiler as the current one for the duration of a call.
+struct ProfScope {
+  explicit ProfScope(Profiler* p) { g_prof = p; }
+  ~ProfScope() { g_prof = nullptr; }
+};
+
+namespace {
+
+// layout of the small device/pinned scratch used by the Krylov methods
+constexpr int kMaxRestart = 128;
+constexpr int kDotH2 = kMaxRestart + 8;        // second Gram-Schmidt pass
+constexpr int kDotW = 2 * (kMaxRestart + 8);   // ||w||^2
+constexpr int kDotY = kDotW + 8;               // least-squares coefficients
+constexpr int kDotNorm = kDotY + kMaxRestart + 8;
+constexpr int kDotSize = kDotNorm + 8;
+
+struct OomError {
+  std::string msg;
+};
+
+template <typename T>
+T* dalloc(size_t count) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw OomError{std::string("cudaMalloc of ") + std::to_string(sizeof(T) * count) + " bytes: " +
+                   cudaGetErrorString(e)};
+  }
+  return (T*)p;
+}
+
+template <typename T>
+T* upload(const T* host, size_t count, cudaStream_t s) {
+  T* d = dalloc<T>(count);
+  if (count) FSI_CUDA_TRY(cudaMemcpyAsync(d, host, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+template <typename T>
+T* upload(const std::vector<T>& v, cudaStream_t s) {
+  return upload(v.data(), v.size(), s);
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+int check_err(Handle& h, cudaStream_t s) {
+  int e = 0;
+  FSI_CUDA_TRY(cudaMemcpyAsync(&e, h.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  if (e) FSI_CUDA_TRY(cudaMemsetAsync(h.d_err, 0, sizeof(int), s));
+  return e;
+}
+
+double norm2_host(Handle& h, const double* x, long n, cudaStream_t s) {
+  dots(h, x, 0, 1, x, n, h.d_dots + kDotNorm, s);
+  double v = 0.0;
+  FSI_CUDA_TRY(cudaMemcpyAsync(&v, h.d_dots + kDotNorm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  return std::sqrt(v);
+}
+
+void alloc_level_vectors(Level& L, bool f32) {
+  const size_t ts = f32 ? 4 : 8;
+  L.x = dalloc<char>(ts * L.bs * (size_t)L.n);
+  L.x2 = dalloc<char>(ts * L.bs * (size_t)L.n);
+  L.b = dalloc<char>(ts * L.bs * (size_t)L.n);
+  L.r = dalloc<char>(ts * L.bs * (size_t)L.n);
+}
+
+void upload_pattern(Level& L, cudaStream_t s) {
+  const HostPattern& P = L.hpat;
+  L.n = (int)P.row_ptr.size() - 1;
+  L.nb = (int)P.col_idx.size();
+  std::vector<int32_t> diag(L.n), brow(L.nb);
+  for (int i = 0; i < L.n; ++i) {
+    diag[i] = find_block(P, i, i);
+    for (int k = P.row_ptr[i]; k < P.row_ptr[i + 1]; ++k) brow[k] = i;
+  }
+  L.row_ptr = upload(P.row_ptr, s);
+  L.col_idx = upload(P.col_idx, s);
+  L.diag_idx = upload(diag, s);
+  L.block_row = upload(brow, s);
+}
+
+// values as T on the device
+void* upload_values(const std::vector<double>& v, bool f32, cudaStream_t s) {
+  if (!f32) return upload(v, s);
+  std::vector<float> f(v.begin(), v.end());
+  float* d = upload(f, s);
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));   // the host staging vector dies here
+  return d;
+}
+
+// Smoothed-aggregation hierarchy from the reference tangent (zero state).
+void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::vector<int32_t>& comp0,
+                     const double* X, cudaStream_t s) {
+  const bool f32 = h.precision == FSI_PREC_FP32_IR;
+  Level& L0 = h.levels[0];
+  // reference tangent, FP64, Dirichlet rows/columns applied
+  double* zero = dalloc<double>(4 * (size_t)h.n_nodes);
+  double* kref = dalloc<double>(16 * (size_t)L0.nb);
+  FSI_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(double) * 4 * h.n_nodes, s));
+  launch_assemble(h, zero, nullptr, nullptr, true, s, kref, 0);
+  HostBsr A0;
+  A0.n = A0.nc = L0.n;
+  A0.br = A0.bc = 4;
+  A0.rp = L0.hpat.row_ptr;
+  A0.ci = L0.hpat.col_idx;
+  A0.v.resize(16 * (size_t)L0.nb);
+  FSI_CUDA_TRY(cudaMemcpyAsync(A0.v.data(), kref, sizeof(double) * A0.v.size(), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFree(zero);
+  cudaFree(kref);
+  if (check_err(h, s) & 1) throw ArgError("reference configuration has an inverted element");
+
+  std::vector<HostLevel> hl;
+  HostCoarse hc;
+  build_sa_hierarchy(A0, free0, X, comp0, std::max(1, h.opts.coarse_max_nodes), std::max(1, h.opts.max_levels),
+                     8, hl, hc);
+  const int nl = (int)hl.size();
+  const size_t ts = f32 ? 4 : 8;
+  for (int l = 1; l < nl; ++l) {
+    Level C;
+    const HostBsr& A = hl[l].A;
+    C.bs = A.br;
+    C.hpat.row_ptr = A.rp;
+    C.hpat.col_idx = A.ci;
+    upload_pattern(C, s);
+    C.vals = upload_values(A.v, f32, s);
+    C.dinv = upload_values(hl[l].Dinv, f32, s);
+    alloc_level_vectors(C, f32);
+    h.levels.push_back(std::move(C));
+  }
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level& L = h.levels[l];
+    const HostLevel& H = hl[l];
+    const int bs = L.bs;
+    L.p_nb = H.P.nb();
+    L.p_rp = upload(H.P.rp, s);
+    L.p_ci = upload(H.P.ci, s);
+    L.p_v = upload_values(H.P.v, f32, s);
+    std::vector<int32_t> brow(L.p_nb);
+    for (int i = 0; i < H.P.n; ++i)
+      for (int q = H.P.rp[i]; q < H.P.rp[i + 1]; ++q) brow[q] = i;
+    L.p_brow = upload(brow, s);
+    L.pt_nb = H.PT.nb();
+    L.pt_rp = upload(H.PT.rp, s);
+    L.pt_ci = upload(H.PT.ci, s);
+    L.pt_v = upload_values(H.PT.v, f32, s);
+    L.pt_src = upload(H.pt_src, s);
+    L.agg = upload(H.agg, s);
+    L.ptent = upload_values(H.Pt, f32, s);
+    L.freem = upload(H.free, s);
+    L.omega_p = H.omega_p;
+    L.w_ptr = upload(H.w_ptr, s);
+    L.w_k = upload(H.w_k, s);
+    L.w_v = dalloc<char>(ts * (size_t)L.p_nb * bs * 7);
+    L.ap_nb = H.AP.nb();
+    L.ap_ptr = upload(H.ap_ptr, s);
+    L.ap_pairs = upload(H.ap_pairs, s);
+    L.ap_v = dalloc<char>(ts * (size_t)L.ap_nb * bs * 7);
+    L.ac_ptr = upload(H.ac_ptr, s);
+    L.ac_pairs = upload(H.ac_pairs, s);
+    L.n_fix = (int)H.fix_blk.size();
+    L.fix_blk = upload(H.fix_blk, s);
+    L.fix_dof = upload(H.fix_dof, s);
+    FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  Coarse& C = h.coarse;
+  C.n_comp = (int)hc.comp_ptr.size() - 1;
+  C.max_dofs = hc.max_dofs;
+  C.comp_ptr = upload(hc.comp_ptr, s);
+  C.inv_off = upload(hc.inv_off, s);
+  C.on_device_factor = true;
+  C.inv = dalloc<char>(ts * hc.inv.size());
+  C.work = dalloc<double>(hc.inv.size());
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+// Per Newton step, from the current tangent: block-Jacobi inverses, smoothed
+// prolongators and Galerkin operators of every level, and the dense inverse
+// of the coarsest operator.
+void amg_numeric(Handle& h, cudaStream_t s) {
+  const bool f32 = h.precision == FSI_PREC_FP32_IR;
+  const int nl = (int)h.levels.size();
+  for (int l = 0; l + 1 < nl; ++l) {
+    launch_block_inverse(h.levels[l], f32, h.d_err, s);
+    launch_galerkin(h.levels[l], h.levels[l + 1], f32, s);
+  }
+  launch_coarse_factor(h, f32, s);
+}
+
+// z = M^-1 v (one V-cycle)
+void precondition(Handle& h, const double* v, double* z, cudaStream_t s) {
+  Level& L0 = h.levels[0];
+  const long n = 4L * L0.n;
+  if (h.precision == FSI_PREC_FP32_IR) {
+    to_float(v, (float*)L0.b, n, s);
+    vcycle<float>(h, 0, s);
+    to_double((const float*)L0.x, z, n, s);
+  } else {
+    FSI_CUDA_TRY(cudaMemcpyAsync(L0.b, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    vcycle<double>(h, 0, s);
+    FSI_CUDA_TRY(cudaMemcpyAsync(z, L0.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+void apply_operator(Handle& h, const double* x, double* y, cudaStream_t s) {
+  launch_spmv_f64acc(h.levels[0], x, y, h.precision == FSI_PREC_FP32_IR, s);
+}
+
+// FGMRES(m), right preconditioned.  Returns iterations; *rel = ||b - A x|| / ||b||.
+int fgmres(Handle& h, const double* b, double* x, double rtol, int maxit, double* rel, cudaStream_t s) {
+  const long n = 4L * h.n_nodes;
+  const int m = h.m;
+  const bool f32 = h.precision == FSI_PREC_FP32_IR;
+  double* V = h.d_V;
+  double* Z = h.d_Z;
+  double* w = h.d_w;
+  double* r = h.d_r;
+  launch_residual_f64(h.levels[0], b, x, r, f32, s);
+  const double bnorm = norm2_host(h, b, n, s);
+  double beta = norm2_host(h, r, n, s);
+  if (bnorm == 0.0) {
+    FSI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    *rel = 0.0;
+    return 0;
+  }
+  const double target = rtol * bnorm;
+  int total = 0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  while (beta > target && total < maxit) {
+    scale_copy(1.0 / beta, r, V, n, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jj = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      precondition(h, vj, zj, s);
+      apply_operator(h, zj, w, s);
+      // classical Gram-Schmidt, twice
+      dots(h, V, n, j + 1, w, n, h.d_dots, s);
+      multi_axpy(h.d_dots, V, j + 1, n, w, -1.0, s);
+      dots(h, V, n, j + 1, w, n, h.d_dots + kDotH2, s);
+      multi_axpy(h.d_dots + kDotH2, V, j + 1, n, w, -1.0, s);
+      dots(h, w, 0, 1, w, n, h.d_dots + kDotW, s);
+      FSI_CUDA_TRY(cudaMemcpyAsync(h.h_dots, h.d_dots, sizeof(double) * (kDotW + 1), cudaMemcpyDeviceToHost, s));
+      FSI_CUDA_TRY(cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h.h_dots[i] + h.h_dots[kDotH2 + i];
+      const double hn = std::sqrt(std::max(h.h_dots[kDotW], 0.0));
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) scale_copy(1.0 / hn, w, V + (size_t)(j + 1) * n, n, s);
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      {
+        double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+        double d = std::hypot(a, bb);
+        cs[j] = d > 0 ? a / d : 1.0;
+        sn[j] = d > 0 ? bb / d : 0.0;
+        H[(size_t)j * m + j] = d;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+      }
+      ++total;
+      jj = j + 1;
+      if (std::fabs(g[j + 1]) <= target || total >= maxit || hn == 0.0) break;
+    }
+    for (int i = jj - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int k = i + 1; k < jj; ++k) acc -= H[(size_t)i * m + k] * y[k];
+      y[i] = acc / H[(size_t)i * m + i];
+    }
+    FSI_CUDA_TRY(cudaMemcpyAsync(h.d_dots + kDotY, y.data(), sizeof(double) * jj, cudaMemcpyHostToDevice, s));
+    multi_axpy(h.d_dots + kDotY, Z, jj, n, x, 1.0, s);
+    launch_residual_f64(h.levels[0], b, x, r, f32, s);
+    beta = norm2_host(h, r, n, s);
+  }
+  *rel = beta / bnorm;
+  return total;
+}
+
+void set_error(Handle* h, const std::string& msg) {
+  if (h) h->last_error = msg;
+}
+
+int linear_solve(Handle& h, const double* b, double* x, double rtol, double* rel, cudaStream_t s) {
+  return fgmres(h, b, x, rtol, h.opts.max_krylov, rel, s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ create / destroy
+static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_material* mats,
+                           const fsi_solver_opts* opts) {
+  if (!mesh || !mats || n_mat <= 0) throw ArgError("mesh and material table are required");
+  if (mesh->n_nodes <= 0 || mesh->n_elems <= 0 || !mesh->X || !mesh->tets || !mesh->mat_id)
+    throw ArgError("mesh needs n_nodes > 0, n_elems > 0, X, tets and mat_id");
+  if (mesh->n_faces > 0 && !mesh->neu_faces) throw ArgError("n_faces > 0 but neu_faces is NULL");
+  const int nn = mesh->n_nodes, ne = mesh->n_elems;
+  bool need_fibre = false;
+  for (int e = 0; e < ne; ++e) {
+    if (mesh->mat_id[e] < 0 || mesh->mat_id[e] >= n_mat) throw ArgError("mat_id out of range at element " + std::to_string(e));
+    for (int a = 0; a < 4; ++a) {
+      int v = mesh->tets[4 * e + a];
+      if (v < 0 || v >= nn) throw ArgError("vertex index out of range at element " + std::to_string(e));
+    }
+    if (mats[mesh->mat_id[e]].model == FSI_MODEL_ARTERY) need_fibre = true;
+  }
+  for (int m = 0; m < n_mat; ++m) {
+    const fsi_material& M = mats[m];
+    if (M.model != FSI_MODEL_MOONEY_RIVLIN && M.model != FSI_MODEL_ARTERY) throw ArgError("unknown material model");
+    if (!(M.kappa > 0) || !(M.c10 >= 0) || (M.model == FSI_MODEL_ARTERY && !(M.k2 > 0)))
+      throw ArgError("material parameters out of range");
+  }
+  if (need_fibre && !mesh->fibre) throw ArgError("artery material needs fibre directions");
+  for (int f = 0; f < mesh->n_faces; ++f)
+    for (int a = 0; a < 3; ++a) {
+      int v = mesh->neu_faces[3 * f + a];
+      if (v < 0 || v >= nn) throw ArgError("face vertex out of range");
+    }
+
+  Handle* hp = new Handle();
+  Handle& h = *hp;
+  fsi_solid_default_opts(&h.opts);
+  if (opts) h.opts = *opts;
+  h.opts.restart = std::min(std::max(h.opts.restart, 1), kMaxRestart);
+  h.m = h.opts.restart;
+  h.precision = h.opts.precision == FSI_PREC_FP32_IR ? FSI_PREC_FP32_IR : FSI_PREC_FP64;
+  const bool f32 = h.precision == FSI_PREC_FP32_IR;
+  h.n_nodes = nn;
+  h.n_elems = ne;
+  h.n_faces = mesh->n_faces;
+  h.n_mat = n_mat;
+  cudaStream_t s = nullptr;
+  FSI_CUDA_TRY(cudaStreamCreateWithFlags(&h.stream, cudaStreamNonBlocking));
+  s = h.stream;
+
+  // colouring and colour-major element order (stable in element index)
+  h.n_colours = colour_elements(nn, ne, mesh->tets, h.colour_host);
+  h.colour_ptr.assign(h.n_colours + 1, 0);
+  for (int e = 0; e < ne; ++e) h.colour_ptr[h.colour_host[e] + 1]++;
+  for (int c = 0; c < h.n_colours; ++c) h.colour_ptr[c + 1] += h.colour_ptr[c];
+  h.elem_perm_host.resize(ne);
+  {
+    std::vector<int32_t> fill(h.colour_ptr.begin(), h.colour_ptr.end() - 1);
+    for (int e = 0; e < ne; ++e) h.elem_perm_host[fill[h.colour_host[e]]++] = e;
+  }
+  // level-0 pattern and element -> block map
+  h.levels.resize(1);
+  Level& L0 = h.levels[0];
+  element_pattern(nn, ne, mesh->tets, L0.hpat);
+  std::vector<int32_t> conn(4 * (size_t)ne), slot(16 * (size_t)ne), matp(ne);
+  std::vector<double> fib(6 * (size_t)ne, 0.0);
+  for (int k = 0; k < ne; ++k) {
+    const int e = h.elem_perm_host[k];
+    for (int a = 0; a < 4; ++a) conn[4 * k + a] = mesh->tets[4 * e + a];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) slot[16 * k + 4 * a + b] = find_block(L0.hpat, conn[4 * k + a], conn[4 * k + b]);
+    matp[k] = mesh->mat_id[e];
+    if (mesh->fibre)
+      for (int q = 0; q < 6; ++q) fib[6 * k + q] = mesh->fibre[6 * (size_t)e + q];
+  }
+  std::vector<double> mt(8 * (size_t)n_mat);
+  for (int m = 0; m < n_mat; ++m) {
+    const fsi_material& M = mats[m];
+    double mul = M.model == FSI_MODEL_ARTERY ? 2.0 * (M.c10 + M.k1 / (2.0 * M.k2)) : 2.0 * (M.c10 + M.c01);
+    double row[8] = {(double)M.model, M.c10, M.c01, M.k1, M.k2, M.kappa, M.rho, mul};
+    for (int q = 0; q < 8; ++q) mt[8 * m + q] = row[q];
+  }
+  std::vector<uint8_t> dmask(4 * (size_t)nn, 0);
+  if (mesh->dir_mask)
+    for (size_t k = 0; k < dmask.size(); ++k) dmask[k] = mesh->dir_mask[k] ? 1 : 0;
+  std::vector<uint8_t> free0(dmask.size());
+  for (size_t k = 0; k < dmask.size(); ++k) free0[k] = dmask[k] ? 0 : 1;
+  // node -> face incidence for the deterministic load gather
+  std::vector<int32_t> nfp(nn + 1, 0), nfi(3 * (size_t)std::max(mesh->n_faces, 0));
+  for (int f = 0; f < mesh->n_faces; ++f)
+    for (int a = 0; a < 3; ++a) nfp[mesh->neu_faces[3 * f + a] + 1]++;
+  for (int i = 0; i < nn; ++i) nfp[i + 1] += nfp[i];
+  {
+    std::vector<int32_t> fill(nfp.begin(), nfp.end() - 1);
+    for (int f = 0; f < mesh->n_faces; ++f)
+      for (int a = 0; a < 3; ++a) nfi[fill[mesh->neu_faces[3 * f + a]]++] = 3 * f + a;
+  }
+  std::vector<int32_t> comp(nn, 0);
+  if (mesh->seg_node)
+    for (int i = 0; i < nn; ++i) comp[i] = mesh->seg_node[i];
+  for (int i = 1; i < nn; ++i)
+    if (comp[i] < comp[i - 1]) throw ArgError("seg_node must be non-decreasing (segments contiguous)");
+  h.n_seg = nn ? comp[nn - 1] + 1 : 1;
+
+  h.d_conn = upload(conn, s);
+  h.d_slot = upload(slot, s);
+  h.d_mat = upload(matp, s);
+  h.d_fibre = upload(fib, s);
+  h.d_mats = upload(mt, s);
+  h.d_X = upload(mesh->X, 3 * (size_t)nn, s);
+  h.d_dir_mask = upload(dmask, s);
+  h.d_faces = upload(mesh->neu_faces ? mesh->neu_faces : (const int32_t*)nullptr,
+                     mesh->neu_faces ? 3 * (size_t)mesh->n_faces : 0, s);
+  h.d_nf_ptr = upload(nfp, s);
+  h.d_nf_idx = upload(nfi, s);
+  h.d_seg_node = upload(comp, s);
+  h.d_err = dalloc<int>(1);
+  FSI_CUDA_TRY(cudaMemsetAsync(h.d_err, 0, sizeof(int), s));
+  h.d_geo = dalloc<double>(16 * (size_t)ne);
+  launch_geometry(h, s);
+  if (check_err(h, s) & 1) throw ArgError("an element has non-positive reference volume");
+
+  upload_pattern(L0, s);
+  L0.bs = 4;
+  L0.cmask = h.d_dir_mask;
+  L0.vals = dalloc<char>((f32 ? 4 : 8) * 16 * (size_t)L0.nb);
+  L0.dinv = dalloc<char>((f32 ? 4 : 8) * 16 * (size_t)L0.n);
+  alloc_level_vectors(L0, f32);
+  build_hierarchy(h, free0, comp, mesh->X, s);
+
+  const size_t ndof = 4 * (size_t)nn;
+  h.d_V = dalloc<double>((size_t)(h.m + 1) * ndof);
+  h.d_Z = dalloc<double>((size_t)h.m * ndof);
+  h.d_w = dalloc<double>(ndof);
+  h.d_r = dalloc<double>(ndof);
+  h.d_t = dalloc<double>(ndof);
+  h.d_t2 = dalloc<double>(ndof);
+  h.d_t3 = dalloc<double>(ndof);
+  h.d_res = dalloc<double>(ndof);
+  h.d_state_tmp = dalloc<double>(ndof);
+  h.d_fext = dalloc<double>(3 * (size_t)nn);
+  FSI_CUDA_TRY(cudaMemsetAsync(h.d_fext, 0, sizeof(double) * 3 * nn, s));
+  h.red_blocks = 2 * 152;
+  h.d_partial = dalloc<double>((size_t)h.red_blocks * (kMaxRestart + 1));
+  h.d_dots = dalloc<double>(kDotSize);
+  FSI_CUDA_TRY(cudaMallocHost((void**)&h.h_dots, sizeof(double) * kDotSize));
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  return hp;
+}
+
+static void destroy_impl(Handle* hp) {
+  if (!hp) return;
+  Handle& h = *hp;
+  if (h.stream) cudaStreamSynchronize(h.stream);
+  for (size_t l = 0; l < h.levels.size(); ++l) {
+    Level& L = h.levels[l];
+    for (void* p : {(void*)L.row_ptr, (void*)L.col_idx, (void*)L.diag_idx, (void*)L.block_row, L.vals, L.dinv,
+                    (void*)L.p_rp, (void*)L.p_ci, L.p_v, (void*)L.pt_rp, (void*)L.pt_ci, L.pt_v, L.x, L.x2, L.b,
+                    L.r, (void*)L.agg, L.ptent, (void*)L.freem, (void*)L.p_brow, (void*)L.w_ptr, (void*)L.w_k,
+                    L.w_v, (void*)L.pt_src, (void*)L.ap_ptr, (void*)L.ap_pairs, L.ap_v, (void*)L.ac_ptr,
+                    (void*)L.ac_pairs, (void*)L.fix_blk, (void*)L.fix_dof})
+      dfree(p);
+  }
+  for (void* p : {(void*)h.coarse.comp_ptr, (void*)h.coarse.inv_off, h.coarse.inv, (void*)h.coarse.work,
+                  (void*)h.d_conn, (void*)h.d_geo, (void*)h.d_fibre, (void*)h.d_mat, (void*)h.d_slot,
+                  (void*)h.d_mats, (void*)h.d_X, (void*)h.d_dir_mask, (void*)h.d_faces, (void*)h.d_nf_ptr,
+                  (void*)h.d_nf_idx, (void*)h.d_seg_node, (void*)h.d_err, (void*)h.d_V, (void*)h.d_Z,
+                  (void*)h.d_w, (void*)h.d_r, (void*)h.d_t, (void*)h.d_t2, (void*)h.d_t3, (void*)h.d_partial,
+                  (void*)h.d_dots, (void*)h.d_xs, (void*)h.d_ys, (void*)h.d_fext, (void*)h.d_state_tmp,
+                  (void*)h.d_res})
+    dfree(p);
+  if (h.h_dots) cudaFreeHost(h.h_dots);
+  for (cudaEvent_t e : h.prof.pool) cudaEventDestroy(e);
+  if (h.stream) cudaStreamDestroy(h.stream);
+  delete hp;
+}
+
+// ------------------------------------------------------------------ Newton
+static int assemble_checked(Handle& h, const double* state, const double* hist, double* res, bool tangent,
+                            cudaStream_t s) {
+  launch_assemble(h, state, hist, res, tangent, s);
+  int e = check_err(h, s);
+  if (e & 1) return FSI_ERR_INVERTED;
+  return FSI_OK;
+}
+
+static int newton_iterate(Handle& h, double* state, const fsi_load* load, double rn, double eps1, fsi_info* info,
+                          cudaStream_t s) {
+  const long n = 4L * h.n_nodes;
+  const double* hist = load ? load->hist : nullptr;
+  int st = assemble_checked(h, state, hist, nullptr, true, s);
+  if (st) return st;
+  amg_numeric(h, s);
+  int e = check_err(h, s);
+  if (e & 8) throw CudaError("singular coarsest-level operator");
+  scale_copy(-1.0, h.d_res, h.d_t, n, s);
+  FSI_CUDA_TRY(cudaMemsetAsync(h.d_t2, 0, sizeof(double) * n, s));
+  double rel = 0.0;
+  int its = linear_solve(h, h.d_t, h.d_t2, eps1, &rel, s);
+  axpy(1.0, h.d_t2, state, n, s);
+  if (info) {
+    info->krylov_its_total += its;
+    info->krylov_its_last = its;
+    info->lin_res = rel;
+    info->inc_norm = norm2_host(h, h.d_t2, n, s);
+  }
+  (void)rn;
+  if (rel > h.opts.krylov_rtol * 1e3 && its >= h.opts.max_krylov) return FSI_ERR_NOT_CONVERGED;
+  return FSI_OK;
+}
+
+static int solve_impl(Handle& h, double* state, const fsi_load* load, const double* guess, fsi_info* info,
+                      cudaStream_t s) {
+  const long n = 4L * h.n_nodes;
+  fsi_info loc{};
+  if (!info) info = &loc;
+  *info = fsi_info{};
+  info->n_levels = (int)h.levels.size();
+  if (load && load->dir_values) launch_set_dirichlet_values(h, state, load->dir_values, s);
+  launch_external_force(h, load, s);
+  const double* hist = load ? load->hist : nullptr;
+  int st = assemble_checked(h, state, hist, h.d_res, false, s);
+  if (st) return st;
+  const double r0 = norm2_host(h, h.d_res, n, s);
+  double rn = r0;
+  info->res0 = r0;
+  if (guess) {
+    FSI_CUDA_TRY(cudaMemcpyAsync(h.d_state_tmp, state, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    FSI_CUDA_TRY(cudaMemcpyAsync(h.d_t3, guess, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    mask_vector(h.d_dir_mask, h.d_t3, n, s);
+    axpy(1.0, h.d_t3, h.d_state_tmp, n, s);
+    int st2 = assemble_checked(h, h.d_state_tmp, hist, h.d_t, false, s);
+    double rg = st2 ? INFINITY : norm2_host(h, h.d_t, n, s);
+    if (rg <= r0) {
+      FSI_CUDA_TRY(cudaMemcpyAsync(state, h.d_state_tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      FSI_CUDA_TRY(cudaMemcpyAsync(h.d_res, h.d_t, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      rn = rg;
+      info->guess_accepted = 1;
+    }
+  }
+  double eps_prev = 1.0;
+  int k = 0;
+  for (;; ++k) {
+    if (r0 == 0.0 || rn <= h.opts.newton_rtol * r0) break;
+    if (k >= h.opts.max_newton) {
+      info->newton_its = k;
+      info->res = rn;
+      return FSI_ERR_NOT_CONVERGED;
+    }
+    double eps1 = h.opts.krylov_rtol;
+    if (h.opts.adaptive_tol) eps1 = std::max(h.opts.krylov_rtol, std::min(0.1, eps_prev * eps_prev));
+    st = newton_iterate(h, state, load, rn, eps1, info, s);
+    if (st) {
+      info->newton_its = k + 1;
+      return st;
+    }
+    st = assemble_checked(h, state, hist, h.d_res, false, s);
+    if (st) {
+      info->newton_its = k + 1;
+      return st;
+    }
+    double rnew = norm2_host(h, h.d_res, n, s);
+    eps_prev = rnew / std::max(rn, 1e-300);
+    rn = rnew;
+  }
+  info->newton_its = k;
+  info->res = rn;
+  return FSI_OK;
+}
+
+}  // namespace fsi
+
+// ------------------------------------------------------------------ C ABI
+using fsi::Handle;
+
+struct fsi_solid_s {
+  Handle h;
+};
+
+#define FSI_GUARD_BEGIN try {
+#define FSI_GUARD_END(hptr)                                  \
+  }                                                          \
+  catch (const fsi::ArgError& e) {                           \
+    fsi::set_error(hptr, e.msg);                             \
+    return FSI_ERR_ARG;                                      \
+  }                                                          \
+  catch (const fsi::CudaError& e) {                          \
+    fsi::set_error(hptr, e.msg);                             \
+    return FSI_ERR_CUDA;                                     \
+  }                                                          \
+  catch (const fsi::OomError& e) {                           \
+    fsi::set_error(hptr, e.msg);                             \
+    return FSI_ERR_OOM;                                      \
+  }                                                          \
+  catch (const std::bad_alloc&) {                            \
+    fsi::set_error(hptr, "host allocation failed");          \
+    return FSI_ERR_OOM;                                      \
+  }
+
+static inline Handle* H(fsi_solid_t h) { return reinterpret_cast<Handle*>(h); }
+#define FSI_PROF(h) fsi::ProfScope fsi_prof_scope_(&(h)->prof)
+static inline cudaStream_t S(Handle* h, void* stream) { return stream ? (cudaStream_t)stream : h->stream; }
+
+static thread_local std::string g_create_error;
+
+extern "C" {
+
+void fsi_solid_default_opts(fsi_solver_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = FSI_PREC_FP64;
+  o->krylov = FSI_KRYLOV_FGMRES;
+  o->restart = 100;
+  o->max_krylov = 300;
+  o->max_newton = 25;
+  o->smoother = FSI_SMOOTHER_JACOBI;
+  o->nu_pre = 3;
+  o->nu_post = 3;
+  o->cheb_degree = 3;
+  o->coarse_max_nodes = 16;
+  o->max_levels = 12;
+  o->use_pspg = 1;
+  o->adaptive_tol = 0;
+  o->use_graphs = 0;
+  o->omega = 0.7;
+  o->newton_rtol = 1e-8;
+  o->krylov_rtol = 1e-8;
+  o->fibre_factor = 2.0;
+  o->inertia_coef = 0.0;
+}
+
+fsi_status fsi_solid_create(const fsi_mesh_desc* mesh, int32_t n_mat, const fsi_material* mats,
+                            const fsi_solver_opts* opts, fsi_solid_t* out) {
+  if (!out) return FSI_ERR_ARG;
+  *out = nullptr;
+  Handle* hp = nullptr;
+  try {
+    hp = fsi::create_impl(mesh, n_mat, mats, opts);
+    *out = reinterpret_cast<fsi_solid_t>(hp);
+    return FSI_OK;
+  } catch (const fsi::ArgError& e) {
+    g_create_error = e.msg;
+    return FSI_ERR_ARG;
+  } catch (const fsi::CudaError& e) {
+    g_create_error = e.msg;
+    return FSI_ERR_CUDA;
+  } catch (const fsi::OomError& e) {
+    g_create_error = e.msg;
+    return FSI_ERR_OOM;
+  } catch (const std::bad_alloc&) {
+    g_create_error = "host allocation failed";
+    return FSI_ERR_OOM;
+  }
+}
+
+fsi_status fsi_solid_destroy(fsi_solid_t h) {
+  fsi::destroy_impl(H(h));
+  return FSI_OK;
+}
+
+fsi_status fsi_solid_residual_tangent(fsi_solid_t hh, const double* state, const fsi_load* load, double* residual,
+                                      int32_t want_tangent, void* stream) {
+  Handle* h = H(hh);
+  if (!h || !state) return FSI_ERR_ARG;
+  FSI_GUARD_BEGIN
+  FSI_PROF(h);
+  cudaStream_t s = S(h, stream);
+  fsi::launch_external_force(*h, load, s);
+  int st = fsi::assemble_checked(*h, state, load ? load->hist : nullptr, residual, want_tangent != 0, s);
+  if (st) {
+    fsi::set_error(h, "inverted or non-finite element");
+    return (fsi_status)st;
+  }
+  return FSI_OK;
+  FSI_GUARD_END(h)
+}
+
+fsi_status fsi_solid_get_bsr(fsi_solid_t hh, const int32_t** row_ptr, const int32_t** col_idx, const void** vals,
+                             int32_t* dtype, int32_t* n_blocks) {
+  Handle* h = H(hh);
+  if (!h) return FSI_ERR_ARG;
+  const fsi::Level& L = h->levels[0];
+  if (row_ptr) *row_ptr = L.row_ptr;
+  if (col_idx) *col_idx = L.col_idx;
+  if (vals) *vals = L.vals;
+  if (dtype) *dtype = h->precision == FSI_PREC_FP32_IR ? 1 : 0;
+  if (n_blocks) *n_blocks = L.nb;
+  return FSI_OK;
+}
+
+fsi_status fsi_solid_spmv(fsi_solid_t hh, const double* x, double* y, void* stream) {
+  Handle* h = H(hh);
+  if (!h || !x || !y) return FSI_ERR_ARG;
+  FSI_GUARD_BEGIN
+  FSI_PROF(h);
+  cudaStream_t s = S(h, stream);
+  fsi::apply_operator(*h, x, y, s);
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  return FSI_OK;
+  FSI_GUARD_END(h)
+}
+
+fsi_status fsi_solid_linear_solve(fsi_solid_t hh, const double* b, double* x, fsi_info* info, void* stream) {
+  Handle* h = H(hh);
+  if (!h || !b || !x) return FSI_ERR_ARG;
+  FSI_GUARD_BEGIN
+  FSI_PROF(h);
+  cudaStream_t s = S(h, stream);
+  fsi::amg_numeric(*h, s);
+  if (fsi::check_err(*h, s) & 8) throw fsi::CudaError("singular coarsest-level operator");
+  double rel = 0.0;
+  int its = fsi::linear_solve(*h, b, x, h->opts.krylov_rtol, &rel, s);
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    *info = fsi_info{};
+    info->krylov_its_total = its;
+    info->krylov_its_last = its;
+    info->lin_res = rel;
+    info->n_levels = (int)h->levels.size();
+  }
+  if (rel > h->opts.krylov_rtol) {
+    fsi::set_error(h, "Krylov iteration cap reached");
+    if (info) info->status = FSI_ERR_NOT_CONVERGED;
+    return FSI_ERR_NOT_CONVERGED;
+  }
+  return FSI_OK;
+  FSI_GUARD_END(h)
+}
+
+fsi_status fsi_solid_newton_step(fsi_solid_t hh, double* state, const fsi_load* load, fsi_info* info, void* stream) {
+  Handle* h = H(hh);
+  if (!h || !state) return FSI_ERR_ARG;
+  FSI_GUARD_BEGIN
+  FSI_PROF(h);
+  cudaStream_t s = S(h, stream);
+  fsi_info loc{};
+  if (!info) info = &loc;
+  *info = fsi_info{};
+  info->n_levels = (int)h->levels.size();
+  const long n = 4L * h->n_nodes;
+  fsi::launch_external_force(*h, load, s);
+  int st = fsi::assemble_checked(*h, state, load ? load->hist : nullptr, h->d_res, false, s);
+  if (st) return (fsi_status)st;
+  info->res0 = fsi::norm2_host(*h, h->d_res, n, s);
+  st = fsi::newton_iterate(*h, state, load, info->res0, h->opts.krylov_rtol, info, s);
+  info->newton_its = 1;
+  info->status = st;
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  return (fsi_status)st;
+  FSI_GUARD_END(h)
+}
+
+fsi_status fsi_solid_solve(fsi_solid_t hh, double* state, const fsi_load* load, const double* guess, fsi_info* info,
+                           void* stream) {
+  Handle* h = H(hh);
+  if (!h || !state) return FSI_ERR_ARG;
+  FSI_GUARD_BEGIN
+  FSI_PROF(h);
+  cudaStream_t s = S(h, stream);
+  int st = fsi::solve_impl(*h, state, load, guess, info, s);
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) info->status = st;
+  if (st) fsi::set_error(h, st == FSI_ERR_INVERTED ? "inverted or non-finite element" : "Newton did not converge");
+  return (fsi_status)st;
+  FSI_GUARD_END(h)
+}
+
+fsi_status fsi_solid_get_colouring(fsi_solid_t hh, int32_t* colour_out, int32_t* n_colours) {
+  Handle* h = H(hh);
+  if (!h) return FSI_ERR_ARG;
+  if (colour_out) std::memcpy(colour_out, h->colour_host.data(), sizeof(int32_t) * h->n_elems);
+  if (n_colours) *n_colours = h->n_colours;
+  return FSI_OK;
+}
+
+fsi_status fsi_solid_get_levels(fsi_solid_t hh, int32_t* nodes_out, int32_t* blocks_out, int32_t capacity,
+                                int32_t* n_levels) {
+  Handle* h = H(hh);
+  if (!h) return FSI_ERR_ARG;
+  int nl = (int)h->levels.size();
+  if (n_levels) *n_levels = nl;
+  for (int l = 0; l < nl && l < capacity; ++l) {
+    if (nodes_out) nodes_out[l] = h->levels[l].n;
+    if (blocks_out) blocks_out[l] = h->levels[l].nb;
+  }
+  return FSI_OK;
+}
+
+int64_t fsi_solid_launch_count(void) { return (int64_t)fsi::g_launches; }
+
+fsi_status fsi_solid_kernel_timing(fsi_solid_t hh, int32_t enable, double* ms_out, int64_t* launches_out) {
+  Handle* h = H(hh);
+  if (!h) return FSI_ERR_ARG;
+  fsi::Profiler& p = h->prof;
+  for (int c = 0; c < FSI_KC_COUNT; ++c) {
+    if (ms_out) ms_out[c] = 0.0;
+    if (launches_out) launches_out[c] = 0;
+  }
+  for (size_t q = 0; q < p.used; ++q) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(p.pool[2 * q + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, p.pool[2 * q], p.pool[2 * q + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const int c = p.cls[q];
+    if (ms_out) ms_out[c] += ms;
+    if (launches_out) launches_out[c] += 1;
+  }
+  p.used = 0;
+  p.on = enable != 0;
+  return FSI_OK;
+}
+
+const char* fsi_solid_last_error(fsi_solid_t hh) {
+  Handle* h = H(hh);
+  if (!h) return g_create_error.c_str();
+  return h->last_error.c_str();
+}
+
+}  // extern "C"

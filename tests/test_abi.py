@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every symbol include/fsi_solid.h declares
+(no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fsi_solid.h")).read()
+    return sorted(set(re.findall(r"\b(fsi_solid_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1312_5561_gb300 import build
+    if not os.path.exists(build.lib_path()):
+        build.build()
+    return ctypes.CDLL(build.lib_path())
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_lists_every_symbol():
+    from paper_1312_5561_gb300 import binding
+    assert sorted(binding.EXPORTS) == _declared()
+
+
+def test_struct_layouts_match_header():
+    """Sizes of the ctypes mirrors equal the C sizes (checked with the host compiler)."""
+    import subprocess
+    import tempfile
+    from paper_1312_5561_gb300 import binding as b
+    code = ('#include "fsi_solid.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(){printf("%zu %zu %zu %zu %zu %zu\\n",'
+            'sizeof(fsi_mesh_desc),sizeof(fsi_material),sizeof(fsi_solver_opts),sizeof(fsi_load),sizeof(fsi_info),'
+            'offsetof(fsi_solver_opts, omega));}')
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "s.c")
+        open(src, "w").write(code)
+        exe = os.path.join(d, "s")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        sizes = list(map(int, subprocess.check_output([exe]).split()))
+    got = [ctypes.sizeof(b.MeshDesc), ctypes.sizeof(b.MaterialDesc), ctypes.sizeof(b.SolverOpts),
+           ctypes.sizeof(b.LoadDesc), ctypes.sizeof(b.Info), b.SolverOpts.omega.offset]
+    assert got == sizes
+
+
+def test_create_error_is_reported_without_gpu_work(lib):
+    """A NULL mesh is rejected before any CUDA call."""
+    from paper_1312_5561_gb300 import binding as b
+    h = ctypes.c_void_p()
+    st = b.lib.fsi_solid_create(None, 0, None, None, ctypes.byref(h))
+    assert st == -1 and not h.value
+    assert b"required" in b.lib.fsi_solid_last_error(None)

@@ -1,0 +1,227 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (FP64 mode): residual and tangent entries within 1e-12 of the
+largest reference entry of the same block row; linear solves within 1e-10;
+Newton solutions within 1e-8 (relative to the largest entry).  Colouring and
+assembly are compared bit for bit.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from fixtures import artery_layers, artery_tube, cube_uniaxial_bc, kuhn_cube, mooney_rivlin
+from oracle import solid as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _solver(mesh, **kw):
+    from paper_1312_5561_gb300.binding import SolidSolver
+    return SolidSolver(mesh, **kw)
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda", dtype=torch.float64)
+
+
+def _smooth_state(mesh, seed, amp=0.06, pamp=0.3, noise=0.001):
+    rng = np.random.default_rng(seed)
+    s = np.zeros((mesh.n_nodes, 4))
+    s[:, :3] = mesh.X @ (amp * rng.standard_normal((3, 3))).T + noise * rng.standard_normal((mesh.n_nodes, 3))
+    s[:, 3] = pamp * rng.standard_normal(mesh.n_nodes)
+    return s
+
+
+def _bsr_to_csr(row_ptr, col_idx, vals, n):
+    return sp.bsr_matrix((vals.astype(np.float64), col_idx, row_ptr), shape=(4 * n, 4 * n)).tocsr()
+
+
+def _blockrow_rel_err(Kg, Kr, n):
+    """max over block rows of max|Kg - Kr| / max|Kr| within that block row."""
+    D = (Kg - Kr).tocsr()
+    worst = 0.0
+    Ar = abs(Kr).tocsr()
+    Ad = abs(D).tocsr()
+    for i in range(n):
+        sl = slice(4 * i, 4 * i + 4)
+        ref = Ar[sl].max()
+        d = Ad[sl].max()
+        if ref > 0:
+            worst = max(worst, d / ref)
+    return worst
+
+
+MESHES = {
+    "cube_mr": lambda: cube_uniaxial_bc(kuhn_cube(4), stretch=0.1),
+    "tube_artery": lambda: artery_tube(n_theta=16, n_z=6, materials=artery_layers(1.0e3)),
+}
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_residual_and_tangent_parity(name):
+    mesh = MESHES[name]()
+    P = O.Problem(mesh)
+    s = _smooth_state(mesh, 3)
+    pressure = 1.3 if len(mesh.neu_faces) else 0.0
+    from paper_1312_5561_gb300.binding import Load
+    solver = _solver(mesh)
+    R = solver.residual_tangent(_t(s), Load(pressure=pressure)).cpu().numpy()
+    R_ref = P.residual(s, P.external_force(pressure))
+    scale = np.abs(R_ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(R - R_ref) <= 1e-12 * np.maximum(scale, np.abs(R_ref).max() * 1e-3))
+    rp, ci, vals = solver.bsr()
+    Kg = _bsr_to_csr(rp, ci, vals, mesh.n_nodes)
+    Kr = P.tangent(s)
+    assert _blockrow_rel_err(Kg, Kr, mesh.n_nodes) <= 1e-12
+    if name == "tube_artery":
+        # both fibre families were active in part of the mesh
+        g, V, h, mp, fib = P._sub(np.arange(mesh.n_elems))
+        act = O.fibre_activity(s[mesh.tets], g, fib)
+        assert act.any(axis=1).all() and not act.all()
+
+
+def test_assembly_is_bitwise_deterministic_and_colouring_matches():
+    mesh = MESHES["tube_artery"]()
+    s = _t(_smooth_state(mesh, 5))
+    solver = _solver(mesh)
+    R1 = solver.residual_tangent(s).clone()
+    _, _, v1 = solver.bsr()
+    R2 = solver.residual_tangent(s).clone()
+    _, _, v2 = solver.bsr()
+    assert torch.equal(R1, R2)
+    assert np.array_equal(v1.view(np.uint64), v2.view(np.uint64))
+    col, nc = solver.colouring()
+    ref = O.greedy_colouring(mesh.tets, mesh.n_nodes)
+    assert np.array_equal(col, ref) and nc == ref.max() + 1
+
+
+def test_spmv_parity():
+    mesh = MESHES["cube_mr"]()
+    P = O.Problem(mesh)
+    s = _smooth_state(mesh, 9)
+    solver = _solver(mesh)
+    solver.residual_tangent(_t(s))
+    x = np.random.default_rng(1).standard_normal((mesh.n_nodes, 4))
+    y = solver.spmv(_t(x)).cpu().numpy().ravel()
+    y_ref = P.tangent(s) @ x.ravel()
+    assert np.abs(y - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+
+
+@pytest.mark.parametrize("n", [2, 8])
+def test_linear_solve_against_direct(n):
+    """Krylov + AMG result against a direct solve (dense LU for the 2x2x2 cube)."""
+    mesh = cube_uniaxial_bc(kuhn_cube(n), stretch=0.1)
+    P = O.Problem(mesh)
+    s = P.apply_dirichlet(_smooth_state(mesh, 4, amp=0.05), mesh.dir_values(1.0))
+    solver = _solver(mesh, krylov_rtol=1e-13, max_krylov=600)
+    solver.residual_tangent(_t(s))
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal((mesh.n_nodes, 4)) * (mesh.dir_mask == 0)
+    x, info = solver.linear_solve(_t(b))
+    K = P.tangent(s)
+    if n == 2:
+        x_ref = np.linalg.solve(K.toarray(), b.ravel())
+    else:
+        x_ref = spla.spsolve(K.tocsc(), b.ravel())
+    x = x.cpu().numpy().ravel()
+    assert np.abs(x - x_ref).max() <= 1e-10 * np.abs(x_ref).max()
+
+
+def _oracle_ramp(mesh, steps, pressure=0.0, rtol=1e-12):
+    P = O.Problem(mesh)
+    s = np.zeros((mesh.n_nodes, 4))
+    for k in range(1, steps + 1):
+        s = P.apply_dirichlet(s, mesh.dir_values(k / steps))
+        fext = P.external_force(pressure * k / steps) if pressure else None
+        s, _ = P.newton(s, fext=fext, rtol=rtol)
+    return s
+
+
+def test_newton_cube_mooney_rivlin_config():
+    """Unit cube 8^3 x 6 tets, MR c10=0.5 c01=0.1 kappa=1e3, bottom clamped, top
+    stretched 20% in 5 load steps; Newton rtol 1e-10, Krylov rtol 1e-12."""
+    from paper_1312_5561_gb300.binding import Load
+    mesh = cube_uniaxial_bc(kuhn_cube(8, materials=mooney_rivlin(0.5, 0.1, 1.0e3)), stretch=0.2)
+    solver = _solver(mesh, newton_rtol=1e-10, krylov_rtol=1e-12, max_krylov=1000)
+    state = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
+    for k in range(1, 6):
+        info = solver.solve(state, Load(dir_values=_t(mesh.dir_values(k / 5))))
+        assert info.newton_its <= 10
+    ref = _oracle_ramp(mesh, 5)
+    got = state.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_newton_small_artery_pressure_ramp():
+    """Two-layer artery, 64 x 8 x 8 hexes (length 0.5), internal pressure
+    ramped to 0.64 in 4 steps (the same increments as 0 -> 1.6 in 10)."""
+    from paper_1312_5561_gb300.binding import Load
+    mesh = artery_tube(n_theta=64, n_z=8, length=0.5, materials=artery_layers(1.0e3))
+    solver = _solver(mesh, newton_rtol=1e-10, krylov_rtol=1e-12, max_krylov=1000)
+    state = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
+    steps = 4
+    for k in range(1, steps + 1):
+        info = solver.solve(state, Load(pressure=0.16 * k))
+        assert info.newton_its <= 8
+    ref = _oracle_ramp(mesh, steps, pressure=0.64)
+    got = state.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_inverted_element_is_reported():
+    from paper_1312_5561_gb300.binding import FsiError
+    mesh = kuhn_cube(2)
+    solver = _solver(mesh)
+    s = np.zeros((mesh.n_nodes, 4))
+    s[:, 2] = -2.0 * mesh.X[:, 2]            # J < 0 everywhere
+    with pytest.raises(FsiError) as e:
+        solver.residual_tangent(_t(s))
+    assert e.value.status == -4
+    # the handle stays usable
+    R = solver.residual_tangent(_t(np.zeros((mesh.n_nodes, 4))))
+    assert float(R.abs().max()) == 0.0
+
+
+def test_single_element_mesh():
+    from fixtures.meshes import Mesh
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    mesh = Mesh(X=X, tets=np.array([[0, 1, 2, 3]], np.int32), mat_id=np.zeros(1, np.int32),
+                fibre=np.zeros((1, 2, 3)), dir_mask=np.zeros((4, 4), np.uint8),
+                neu_faces=np.zeros((0, 3), np.int32), materials=mooney_rivlin())
+    P = O.Problem(mesh)
+    s = _smooth_state(mesh, 1, amp=0.1)
+    solver = _solver(mesh)
+    R = solver.residual_tangent(_t(s)).cpu().numpy()
+    assert np.abs(R - P.residual(s)).max() <= 1e-12 * np.abs(P.residual(s)).max()
+
+
+# ---------------------------------------------------------------- FP32 tangent + FP32 V-cycle, FP64 residual
+@pytest.mark.parametrize("name", list(MESHES))
+def test_fp32_tangent_parity(name):
+    """FP32 tangent entries within 1e-5 of the largest reference entry of their block row."""
+    mesh = MESHES[name]()
+    P = O.Problem(mesh)
+    s = _smooth_state(mesh, 3)
+    solver = _solver(mesh, precision=1)
+    R = solver.residual_tangent(_t(s)).cpu().numpy()
+    R_ref = P.residual(s)
+    assert np.abs(R - R_ref).max() <= 1e-12 * np.abs(R_ref).max()      # the residual stays FP64
+    rp, ci, vals = solver.bsr()
+    assert vals.dtype == np.float32
+    assert _blockrow_rel_err(_bsr_to_csr(rp, ci, vals, mesh.n_nodes), P.tangent(s), mesh.n_nodes) <= 1e-5
+
+
+def test_fp32_refinement_reaches_fp64_solution():
+    """Newton with the FP32 tangent and V-cycle (iterative refinement by the FP64
+    residual) converges to the FP64 oracle solution within 1e-8."""
+    from paper_1312_5561_gb300.binding import Load
+    mesh = artery_tube(n_theta=64, n_z=8, length=0.5, materials=artery_layers(1.0e5))
+    solver = _solver(mesh, precision=1, newton_rtol=1e-11, krylov_rtol=1e-8, max_krylov=1000)
+    state = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
+    for k in range(1, 3):
+        solver.solve(state, Load(pressure=0.16 * k))
+    ref = _oracle_ramp(mesh, 2, pressure=0.32)
+    got = state.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
