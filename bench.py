@@ -285,6 +285,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--nz", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single", action="store_true", help="skip the plain-FP64 comparison run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -315,7 +316,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world)
     other = None
-    if args.precision == "fp32":
+    if args.precision == "fp32" and not args.single:
         a2 = argparse.Namespace(**vars(args))
         a2.precision = "fp64"
         a2.steps = max(5, args.steps // 2)

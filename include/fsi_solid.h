@@ -99,7 +99,7 @@ typedef struct {
   int32_t use_pspg;         /* 1: PSPG term W_s of Eq. stelas on; 0: off */
   int32_t adaptive_tol;     /* 1: inner tolerance eps_1,k = eps_2,k-1^2 (Sec. 4.4) */
   int32_t use_graphs;       /* 1: capture the V-cycle in a CUDA graph */
-  int32_t pad0;
+  int32_t nu_coarse;        /* smoothing sweeps before / after on every coarser level */
   double omega;             /* block-Jacobi damping */
   double newton_rtol;       /* stop when ||R(v_k)|| <= newton_rtol ||R(v_0)|| */
   double krylov_rtol;       /* relative residual reduction of each linear solve */
@@ -137,7 +137,8 @@ typedef struct {
   double lin_res;            /* relative residual of the last linear solve */
 } fsi_info;
 
-/* Default options: FP64, FGMRES(100), block Jacobi 3+3 sweeps, omega 0.7,
+/* Default options: FP64, FGMRES(100), block Jacobi 4+4 sweeps on the finest
+ * level and 1+1 on coarser levels, omega 0.7,
  * Newton rtol 1e-8, Krylov rtol 1e-8, PSPG on, fibre_factor 2. */
 void fsi_solid_default_opts(fsi_solver_opts* opts);
 

@@ -52,7 +52,7 @@ class SolverOpts(C.Structure):
                 ("max_krylov", C.c_int32), ("max_newton", C.c_int32), ("smoother", C.c_int32),
                 ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("cheb_degree", C.c_int32),
                 ("coarse_max_nodes", C.c_int32), ("max_levels", C.c_int32), ("use_pspg", C.c_int32),
-                ("adaptive_tol", C.c_int32), ("use_graphs", C.c_int32), ("pad0", C.c_int32),
+                ("adaptive_tol", C.c_int32), ("use_graphs", C.c_int32), ("nu_coarse", C.c_int32),
                 ("omega", C.c_double), ("newton_rtol", C.c_double), ("krylov_rtol", C.c_double),
                 ("fibre_factor", C.c_double), ("inertia_coef", C.c_double)]
 

@@ -30,12 +30,14 @@ namespace {
 
 constexpr int kThreads = 128;
 
-__device__ __forceinline__ double dot3(const double* a, const double* b) {
+template <typename T>
+__device__ __forceinline__ T dot3(const T* a, const T* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
 // symmetric 3x3 stored as (00, 11, 22, 01, 02, 12)
-__device__ __forceinline__ void sym_mul_vec(const double* S, const double* v, double* o) {
+template <typename T>
+__device__ __forceinline__ void sym_mul_vec(const T* S, const T* v, T* o) {
   o[0] = S[0] * v[0] + S[3] * v[1] + S[4] * v[2];
   o[1] = S[3] * v[0] + S[1] * v[1] + S[5] * v[2];
   o[2] = S[4] * v[0] + S[5] * v[1] + S[2] * v[2];
@@ -93,36 +95,54 @@ struct ElemIn {
 
 // Residual and (optionally) tangent of one element.  Writes R[a][c] and, when
 // TANGENT, hands each 4x4 block (a, b) to emit(4 a + b, K) as soon as it is formed.
-template <bool TANGENT, typename Emit>
+template <typename TC, bool TANGENT, typename Emit>
 __device__ __forceinline__ bool element_eval(const ElemIn& in, const double* __restrict__ mp,
-                                             const double* __restrict__ fib, double inertia,
-                                             double fibre_factor, double R[4][4], Emit& emit) {
-  const double V = in.V, tauV = in.tauV;
+                                             const double* __restrict__ fibd, double inertia_d,
+                                             double fibre_factor_d, TC R[4][4], Emit& emit) {
+  const TC V = (TC)in.V, tauV = (TC)in.tauV;
   const int model = (int)mp[0];
-  const double c10 = mp[1], c01 = mp[2], k1 = mp[3], k2 = mp[4], kappa = mp[5], rho = mp[6];
+  const TC c10 = (TC)mp[1], c01 = (TC)mp[2], k1 = (TC)mp[3], k2 = (TC)mp[4], kappa = (TC)mp[5], rho = (TC)mp[6];
+  const TC inertia = (TC)inertia_d, fibre_factor = (TC)fibre_factor_d;
+  TC fib[6];
+  for (int q = 0; q < 6; ++q) fib[q] = (TC)fibd[q];
+  TC ug[4][3], pg[4], gg_[4][3], hsg[4][3];
+  for (int a = 0; a < 4; ++a) {
+    pg[a] = (TC)in.p[a];
+    for (int i = 0; i < 3; ++i) {
+      ug[a][i] = (TC)in.u[a][i];
+      gg_[a][i] = (TC)in.g[a][i];
+      hsg[a][i] = (TC)in.hs[a][i];
+    }
+  }
 
-  // ---- kinematics (Sec. 2.3)
-  double H[3][3];
+  // ---- kinematics (Sec. 2.3).  The volumetric terms J - 1, log J and J^{-2/3}
+  // are always formed in FP64 (they decide the pressure coupling at large kappa).
+  double Hd[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
-      H[i][j] = in.u[0][i] * in.g[0][j] + in.u[1][i] * in.g[1][j] + in.u[2][i] * in.g[2][j] +
-                in.u[3][i] * in.g[3][j];
-  const double trH = H[0][0] + H[1][1] + H[2][2];
+      Hd[i][j] = in.u[0][i] * in.g[0][j] + in.u[1][i] * in.g[1][j] + in.u[2][i] * in.g[2][j] +
+                 in.u[3][i] * in.g[3][j];
+  const double trH = Hd[0][0] + Hd[1][1] + Hd[2][2];
   double trHH = 0.0;
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) trHH += H[i][j] * H[j][i];
-  const double detH = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
-                      H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
-                      H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
-  const double Jm1 = trH + 0.5 * (trH * trH - trHH) + detH;   // det(I + H) - 1, no cancellation
-  const double J = 1.0 + Jm1;
-  if (!(J > 0.0) || !isfinite(J)) return false;
-  double F[3][3];
+    for (int j = 0; j < 3; ++j) trHH += Hd[i][j] * Hd[j][i];
+  const double detH = Hd[0][0] * (Hd[1][1] * Hd[2][2] - Hd[1][2] * Hd[2][1]) -
+                      Hd[0][1] * (Hd[1][0] * Hd[2][2] - Hd[1][2] * Hd[2][0]) +
+                      Hd[0][2] * (Hd[1][0] * Hd[2][1] - Hd[1][1] * Hd[2][0]);
+  const double Jm1d = trH + 0.5 * (trH * trH - trHH) + detH;   // det(I + H) - 1, no cancellation
+  const double Jd = 1.0 + Jm1d;
+  if (!(Jd > 0.0) || !isfinite(Jd)) return false;
+  TC H[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? 1.0 : 0.0);
-  double Fi[3][3];   // F^-1 = adj(F) / J
+    for (int j = 0; j < 3; ++j) H[i][j] = (TC)Hd[i][j];
+  const TC Jm1 = (TC)Jm1d;
+  const TC J = (TC)Jd;
+  TC F[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? TC(1.0) : TC(0.0));
+  TC Fi[3][3];   // F^-1 = adj(F) / J
   {
-    const double iJ = 1.0 / J;
+    const TC iJ = TC(1.0) / J;
     Fi[0][0] = (F[1][1] * F[2][2] - F[1][2] * F[2][1]) * iJ;
     Fi[0][1] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * iJ;
     Fi[0][2] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * iJ;
@@ -135,171 +155,172 @@ __device__ __forceinline__ bool element_eval(const ElemIn& in, const double* __r
   }
   // E = (H + H^T + H^T H) / 2, C = I + 2E; symmetric storage (00,11,22,01,02,12)
   const int si[6] = {0, 1, 2, 0, 0, 1}, sj[6] = {0, 1, 2, 1, 2, 2};
-  double E[6], C[6], Ci[6], B[6];
+  TC E[6], C[6], Ci[6], B[6];
   for (int k = 0; k < 6; ++k) {
     int i = si[k], j = sj[k];
-    double hth = H[0][i] * H[0][j] + H[1][i] * H[1][j] + H[2][i] * H[2][j];
-    E[k] = 0.5 * (H[i][j] + H[j][i] + hth);
-    C[k] = 2.0 * E[k] + (i == j ? 1.0 : 0.0);
+    TC hth = H[0][i] * H[0][j] + H[1][i] * H[1][j] + H[2][i] * H[2][j];
+    E[k] = TC(0.5) * (H[i][j] + H[j][i] + hth);
+    C[k] = TC(2.0) * E[k] + (i == j ? TC(1.0) : TC(0.0));
     Ci[k] = Fi[i][0] * Fi[j][0] + Fi[i][1] * Fi[j][1] + Fi[i][2] * Fi[j][2];   // F^-1 F^-T
     B[k] = F[i][0] * F[j][0] + F[i][1] * F[j][1] + F[i][2] * F[j][2];         // F F^T
   }
-  const double I1 = C[0] + C[1] + C[2];
-  const double CC = C[0] * C[0] + C[1] * C[1] + C[2] * C[2] + 2.0 * (C[3] * C[3] + C[4] * C[4] + C[5] * C[5]);
-  const double I2 = 0.5 * (I1 * I1 - CC);
-  const double lj = log1p(Jm1);
-  const double J23 = exp(-(2.0 / 3.0) * lj);   // I3^{-1/3}
-  const double J43 = J23 * J23;                // I3^{-2/3}
+  const TC I1 = C[0] + C[1] + C[2];
+  const TC CC = C[0] * C[0] + C[1] * C[1] + C[2] * C[2] + TC(2.0) * (C[3] * C[3] + C[4] * C[4] + C[5] * C[5]);
+  const TC I2 = TC(0.5) * (I1 * I1 - CC);
+  const double lj = log1p(Jm1d);
+  const double J23d = exp(-(2.0 / 3.0) * lj);
+  const TC J23 = (TC)J23d;                 // I3^{-1/3}
+  const TC J43 = J23 * J23;                // I3^{-2/3}
 
   // ---- isochoric stress S' and dS'/dC coefficients
-  double S[6];
+  TC S[6];
   for (int k = 0; k < 6; ++k) {
-    double d = (si[k] == sj[k]) ? 1.0 : 0.0;
-    S[k] = c10 * J23 * (d - (I1 / 3.0) * Ci[k]) + c01 * J43 * (I1 * d - C[k] - (2.0 / 3.0) * I2 * Ci[k]);
+    TC d = (si[k] == sj[k]) ? TC(1.0) : TC(0.0);
+    S[k] = c10 * J23 * (d - (I1 / TC(3.0)) * Ci[k]) + c01 * J43 * (I1 * d - C[k] - (TC(2.0) / TC(3.0)) * I2 * Ci[k]);
   }
   // m over basis 0:I 1:C 2:Ci 3:A1 4:A2 (symmetric), gamma (Ci.Ci), eta (II)
-  double m[5][5];
+  TC m[5][5];
   for (int x = 0; x < 5; ++x)
-    for (int y = 0; y < 5; ++y) m[x][y] = 0.0;
-  double gam = 0.0, eta = 0.0;
+    for (int y = 0; y < 5; ++y) m[x][y] = TC(0.0);
+  TC gam = TC(0.0), eta = TC(0.0);
   if (TANGENT) {
-    m[0][2] += -c10 * J23 / 3.0;
-    m[2][2] += c10 * J23 * I1 / 9.0;
-    gam += c10 * J23 * I1 / 3.0;
-    m[0][2] += -(2.0 / 3.0) * c01 * J43 * I1;
-    m[1][2] += (2.0 / 3.0) * c01 * J43;
-    m[2][2] += (4.0 / 9.0) * c01 * J43 * I2;
+    m[0][2] += -c10 * J23 / TC(3.0);
+    m[2][2] += c10 * J23 * I1 / TC(9.0);
+    gam += c10 * J23 * I1 / TC(3.0);
+    m[0][2] += -(TC(2.0) / TC(3.0)) * c01 * J43 * I1;
+    m[1][2] += (TC(2.0) / TC(3.0)) * c01 * J43;
+    m[2][2] += (TC(4.0) / TC(9.0)) * c01 * J43 * I2;
     m[0][0] += c01 * J43;
     eta += -c01 * J43;
-    gam += (2.0 / 3.0) * c01 * J43 * I2;
+    gam += (TC(2.0) / TC(3.0)) * c01 * J43 * I2;
   }
-  double af[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  TC af[2][3] = {{0, 0, 0}, {0, 0, 0}};
   if (model == FSI_MODEL_ARTERY) {
     const double J23m1 = expm1(-(2.0 / 3.0) * lj);
     for (int f = 0; f < 2; ++f) {
-      const double* a = fib + 3 * f;
-      double Ca[3], Ea[3];
+      const TC* a = fib + 3 * f;
+      TC Ca[3], Ea[3];
       sym_mul_vec(C, a, Ca);
       sym_mul_vec(E, a, Ea);
-      const double I4 = dot3(a, Ca);
-      const double Jim1 = J23m1 + J23 * 2.0 * dot3(a, Ea);   // J_i - 1 (Eq. arinv46)
-      if (!(Jim1 > 0.0)) continue;                             // fibres act in extension only
+      const TC I4 = dot3(a, Ca);
+      const TC Jim1 = (TC)(J23m1 + J23d * 2.0 * (double)dot3(a, Ea));   // J_i - 1 (Eq. arinv46), FP64
+      if (!(Jim1 > TC(0.0))) continue;                             // fibres act in extension only
       for (int i = 0; i < 3; ++i) af[f][i] = a[i];
-      const double ex = exp(k2 * Jim1 * Jim1);
-      const double beta = fibre_factor * k1 * ex * Jim1;
-      for (int k = 0; k < 6; ++k) S[k] += beta * J23 * (a[si[k]] * a[sj[k]] - (I4 / 3.0) * Ci[k]);
+      const TC ex = exp(k2 * Jim1 * Jim1);
+      const TC beta = fibre_factor * k1 * ex * Jim1;
+      for (int k = 0; k < 6; ++k) S[k] += beta * J23 * (a[si[k]] * a[sj[k]] - (I4 / TC(3.0)) * Ci[k]);
       if (TANGENT) {
-        const double alpha = fibre_factor * k1 * ex * (1.0 + 2.0 * k2 * Jim1 * Jim1);
+        const TC alpha = fibre_factor * k1 * ex * (TC(1.0) + TC(2.0) * k2 * Jim1 * Jim1);
         const int X = 3 + f;
         m[X][X] += alpha * J43;
-        m[X][2] += -alpha * J43 * I4 / 3.0 - beta * J23 / 3.0;
-        m[2][2] += alpha * J43 * I4 * I4 / 9.0 + beta * J23 * I4 / 9.0;
-        gam += beta * J23 * I4 / 3.0;
+        m[X][2] += -alpha * J43 * I4 / TC(3.0) - beta * J23 / TC(3.0);
+        m[2][2] += alpha * J43 * I4 * I4 / TC(9.0) + beta * J23 * I4 / TC(9.0);
+        gam += beta * J23 * I4 / TC(3.0);
       }
     }
   }
 
   // ---- per-node vectors
-  const double pbar = 0.25 * (in.p[0] + in.p[1] + in.p[2] + in.p[3]);
-  double gp[3], ubar[3], hbar[3];
+  const TC pbar = TC(0.25) * (pg[0] + pg[1] + pg[2] + pg[3]);
+  TC gp[3], ubar[3], hbar[3];
   for (int i = 0; i < 3; ++i) {
-    gp[i] = in.p[0] * in.g[0][i] + in.p[1] * in.g[1][i] + in.p[2] * in.g[2][i] + in.p[3] * in.g[3][i];
-    ubar[i] = 0.25 * (in.u[0][i] + in.u[1][i] + in.u[2][i] + in.u[3][i]);
-    hbar[i] = 0.25 * (in.hs[0][i] + in.hs[1][i] + in.hs[2][i] + in.hs[3][i]);
+    gp[i] = pg[0] * gg_[0][i] + pg[1] * gg_[1][i] + pg[2] * gg_[2][i] + pg[3] * gg_[3][i];
+    ubar[i] = TC(0.25) * (ug[0][i] + ug[1][i] + ug[2][i] + ug[3][i]);
+    hbar[i] = TC(0.25) * (hsg[0][i] + hsg[1][i] + hsg[2][i] + hsg[3][i]);
   }
-  double q[3], w[3];
+  TC q[3], w[3];
   for (int i = 0; i < 3; ++i) {
     q[i] = Fi[0][i] * gp[0] + Fi[1][i] * gp[1] + Fi[2][i] * gp[2];   // F^-T grad p
     w[i] = rho * hbar[i] - rho * inertia * ubar[i];
   }
-  double gb[4][3];   // F^-T g_a
+  TC gb[4][3];   // F^-T g_a
   for (int a = 0; a < 4; ++a)
     for (int i = 0; i < 3; ++i)
-      gb[a][i] = Fi[0][i] * in.g[a][0] + Fi[1][i] * in.g[a][1] + Fi[2][i] * in.g[a][2];
-  double FS[3][3];   // F S' (S' symmetric)
+      gb[a][i] = Fi[0][i] * gg_[a][0] + Fi[1][i] * gg_[a][1] + Fi[2][i] * gg_[a][2];
+  TC FS[3][3];   // F S' (S' symmetric)
   for (int i = 0; i < 3; ++i) {
     for (int k = 0; k < 3; ++k) {
-      double s0 = (k == 0) ? S[0] : (k == 1 ? S[3] : S[4]);
-      double s1 = (k == 0) ? S[3] : (k == 1 ? S[1] : S[5]);
-      double s2 = (k == 0) ? S[4] : (k == 1 ? S[5] : S[2]);
+      TC s0 = (k == 0) ? S[0] : (k == 1 ? S[3] : S[4]);
+      TC s1 = (k == 0) ? S[3] : (k == 1 ? S[1] : S[5]);
+      TC s2 = (k == 0) ? S[4] : (k == 1 ? S[5] : S[2]);
       FS[i][k] = F[i][0] * s0 + F[i][1] * s1 + F[i][2] * s2;
     }
   }
 
   // ---- residual (always FP64): R^1_a rows 0..2, R^2_a row 3
-  double usum[3], hsum[3], psum = in.p[0] + in.p[1] + in.p[2] + in.p[3];
+  TC usum[3], hsum[3], psum = pg[0] + pg[1] + pg[2] + pg[3];
   for (int i = 0; i < 3; ++i) {
-    usum[i] = in.u[0][i] + in.u[1][i] + in.u[2][i] + in.u[3][i];
-    hsum[i] = in.hs[0][i] + in.hs[1][i] + in.hs[2][i] + in.hs[3][i];
+    usum[i] = ug[0][i] + ug[1][i] + ug[2][i] + ug[3][i];
+    hsum[i] = hsg[0][i] + hsg[1][i] + hsg[2][i] + hsg[3][i];
   }
-  const double V20 = V / 20.0;
+  const TC V20 = V / TC(20.0);
   for (int a = 0; a < 4; ++a) {
     for (int i = 0; i < 3; ++i) {
-      double fsg = FS[i][0] * in.g[a][0] + FS[i][1] * in.g[a][1] + FS[i][2] * in.g[a][2];
-      R[a][i] = V * (fsg - pbar * J * gb[a][i]) + rho * inertia * V20 * (in.u[a][i] + usum[i]) -
-                rho * V20 * (in.hs[a][i] + hsum[i]);
+      TC fsg = FS[i][0] * gg_[a][0] + FS[i][1] * gg_[a][1] + FS[i][2] * gg_[a][2];
+      R[a][i] = V * (fsg - pbar * J * gb[a][i]) + rho * inertia * V20 * (ug[a][i] + usum[i]) -
+                rho * V20 * (hsg[a][i] + hsum[i]);
     }
-    double wq = (w[0] - J * q[0]) * gb[a][0] + (w[1] - J * q[1]) * gb[a][1] + (w[2] - J * q[2]) * gb[a][2];
-    R[a][3] = -V * Jm1 * 0.25 - V20 * (in.p[a] + psum) / kappa + tauV * wq;
+    TC wq = (w[0] - J * q[0]) * gb[a][0] + (w[1] - J * q[1]) * gb[a][1] + (w[2] - J * q[2]) * gb[a][2];
+    R[a][3] = -V * Jm1 * TC(0.25) - V20 * (pg[a] + psum) / kappa + tauV * wq;
   }
   if (!TANGENT) return true;
 
   // ---- tangent blocks
-  double fv[4][3];   // F g_a
+  TC fv[4][3];   // F g_a
   for (int a = 0; a < 4; ++a)
-    for (int i = 0; i < 3; ++i) fv[a][i] = F[i][0] * in.g[a][0] + F[i][1] * in.g[a][1] + F[i][2] * in.g[a][2];
-  double Fa[2][3];   // F a_i
+    for (int i = 0; i < 3; ++i) fv[a][i] = F[i][0] * gg_[a][0] + F[i][1] * gg_[a][1] + F[i][2] * gg_[a][2];
+  TC Fa[2][3];   // F a_i
   for (int f = 0; f < 2; ++f)
     for (int i = 0; i < 3; ++i) Fa[f][i] = F[i][0] * af[f][0] + F[i][1] * af[f][1] + F[i][2] * af[f][2];
   // pressure geometric term folded into the C^-1 (x) C^-1 coefficient and the swap term
-  m[2][2] += -0.5 * pbar * J;
+  m[2][2] += -TC(0.5) * pbar * J;
   // symmetric completion
   for (int x = 0; x < 5; ++x)
     for (int y = x + 1; y < 5; ++y) {
-      double s = m[x][y] + m[y][x];
+      TC s = m[x][y] + m[y][x];
       m[x][y] = s;
       m[y][x] = s;
     }
   // w_X(b) = F X g_b, z_X(b) = sum_Y m_XY w_Y(b)
-  double z[4][5][3];
-  double wv[4][5][3];
+  TC z[4][5][3];
+  TC wv[4][5][3];
   for (int b = 0; b < 4; ++b) {
-    double Bf[3];
+    TC Bf[3];
     sym_mul_vec(B, fv[b], Bf);
     for (int i = 0; i < 3; ++i) {
       wv[b][0][i] = fv[b][i];
       wv[b][1][i] = Bf[i];
       wv[b][2][i] = gb[b][i];
-      wv[b][3][i] = Fa[0][i] * dot3(af[0], in.g[b]);
-      wv[b][4][i] = Fa[1][i] * dot3(af[1], in.g[b]);
+      wv[b][3][i] = Fa[0][i] * dot3(af[0], gg_[b]);
+      wv[b][4][i] = Fa[1][i] * dot3(af[1], gg_[b]);
     }
     for (int x = 0; x < 5; ++x)
       for (int i = 0; i < 3; ++i) {
-        double acc = 0.0;
+        TC acc = TC(0.0);
         for (int y = 0; y < 5; ++y) acc += m[x][y] * wv[b][y][i];
-        z[b][x][i] = 2.0 * V * acc;
+        z[b][x][i] = TC(2.0) * V * acc;
       }
   }
-  double Sg[4][3];
-  for (int b = 0; b < 4; ++b) sym_mul_vec(S, in.g[b], Sg[b]);
-  double qg[4], wg[4];
+  TC Sg[4][3];
+  for (int b = 0; b < 4; ++b) sym_mul_vec(S, gg_[b], Sg[b]);
+  TC qg[4], wg[4];
   for (int a = 0; a < 4; ++a) {
     qg[a] = dot3(q, gb[a]);
     wg[a] = dot3(w, gb[a]);
   }
-  const double Vswap = V * (gam + pbar * J);
-  const double Vgam = V * gam, Veta = V * eta;
-  const double c_in = rho * inertia;
+  const TC Vswap = V * (gam + pbar * J);
+  const TC Vgam = V * gam, Veta = V * eta;
+  const TC c_in = rho * inertia;
   for (int a = 0; a < 4; ++a) {
     for (int b = 0; b < 4; ++b) {
-      const double Mab = V20 * (a == b ? 2.0 : 1.0);
-      const double gg = dot3(in.g[a], in.g[b]);
-      const double gbgb = dot3(gb[a], gb[b]);
-      const double diag = V * dot3(in.g[a], Sg[b]) + Vgam * gbgb + c_in * Mab;
-      double K[4][4];
+      const TC Mab = V20 * (a == b ? TC(2.0) : TC(1.0));
+      const TC gg = dot3(gg_[a], gg_[b]);
+      const TC gbgb = dot3(gb[a], gb[b]);
+      const TC diag = V * dot3(gg_[a], Sg[b]) + Vgam * gbgb + c_in * Mab;
+      TC K[4][4];
       for (int i = 0; i < 3; ++i) {
         for (int k = 0; k < 3; ++k) {
-          double v = 0.0;
+          TC v = TC(0.0);
           for (int x = 0; x < 5; ++x) v += wv[a][x][i] * z[b][x][k];
           v += Vswap * gb[b][i] * gb[a][k] + Veta * fv[b][i] * fv[a][k];
           int sk = (i == k) ? i : (i + k == 1 ? 3 : (i + k == 2 ? 4 : 5));
@@ -307,11 +328,11 @@ __device__ __forceinline__ bool element_eval(const ElemIn& in, const double* __r
           if (i == k) v += diag;
           K[i][k] = v;
         }
-        K[i][3] = -0.25 * V * J * gb[a][i];
+        K[i][3] = -TC(0.25) * V * J * gb[a][i];
       }
-      const double ca = tauV * (-0.25 * c_in - wg[b] + J * qg[b]);
-      const double cb = -0.25 * V * J - tauV * J * qg[a];
-      const double cq = tauV * J * gbgb;
+      const TC ca = tauV * (-TC(0.25) * c_in - wg[b] + J * qg[b]);
+      const TC cb = -TC(0.25) * V * J - tauV * J * qg[a];
+      const TC cq = tauV * J * gbgb;
       for (int k = 0; k < 3; ++k) K[3][k] = cb * gb[b][k] + ca * gb[a][k] + cq * q[k];
       K[3][3] = -Mab / kappa - tauV * J * gbgb;
       emit(4 * a + b, K);
@@ -324,7 +345,8 @@ template <typename T>
 struct BsrEmit {
   T* vals;
   const int32_t* slot;
-  __device__ __forceinline__ void operator()(int ab, const double (&K)[4][4]) const {
+  template <typename TC>
+  __device__ __forceinline__ void operator()(int ab, const TC (&K)[4][4]) const {
     T* v = vals + 16 * (size_t)slot[ab];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -333,7 +355,9 @@ struct BsrEmit {
   }
 };
 
-template <typename T, bool TANGENT>
+// T: storage type of the tangent; TC: arithmetic type of the element math
+// (the volumetric J terms are FP64 in both cases).
+template <typename T, typename TC, bool TANGENT>
 __global__ void __launch_bounds__(kThreads) assemble_kernel(
     int e0, int e1, const int32_t* __restrict__ conn, const double* __restrict__ geo,
     const double* __restrict__ fibre, const int32_t* __restrict__ mat, const double* __restrict__ mats,
@@ -358,16 +382,16 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(
   in.tauV = ge[13];
   const double* mp = mats + 8 * mat[e];
   const double* fib = fibre + 6 * (size_t)e;
-  double R[4][4];
+  TC R[4][4];
   BsrEmit<T> emit{vals, slot + 16 * (size_t)e};
-  if (!element_eval<TANGENT>(in, mp, fib, inertia, fibre_factor, R, emit)) {
+  if (!element_eval<TC, TANGENT>(in, mp, fib, inertia, fibre_factor, R, emit)) {
     atomicOr(err, 1);
     return;
   }
   if (res) {
     for (int a = 0; a < 4; ++a) {
       double* r = res + 4 * (size_t)nid[a];
-      for (int c = 0; c < 4; ++c) r[c] += R[a][c];
+      for (int c = 0; c < 4; ++c) r[c] += (double)R[a][c];
     }
   }
 }
@@ -471,23 +495,25 @@ void launch_assemble(Handle& h, const double* state, const double* hist, double*
   if (residual)
     FSI_LAUNCH(fsi::KC_OTHER, s, init_residual_kernel<<<blocks_for(h.n_nodes, 256), 256, 0, s>>>(h.n_nodes, h.d_fext, residual));
   if (want_tangent) FSI_CUDA_TRY(cudaMemsetAsync(vals, 0, (size_t)L0.nb * 16 * (f32 ? 4 : 8), s));
+  // FP32 tangents are formed by an FP32 kernel; the residual always comes from the FP64 kernel
+  const bool split = want_tangent && f32;
   for (int c = 0; c < h.n_colours; ++c) {
     int e0 = h.colour_ptr[c], e1 = h.colour_ptr[c + 1];
     if (e1 <= e0) continue;
     int nbk = blocks_for(e1 - e0, kThreads);
-    if (want_tangent) {
-      if (f32)
-        FSI_LAUNCH(fsi::KC_TANGENT, s, assemble_kernel<float, true><<<nbk, kThreads, 0, s>>>(e0, e1, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats,
-                                                                state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
-                                                                h.d_slot, (float*)vals, residual, h.d_err));
-      else
-        FSI_LAUNCH(fsi::KC_TANGENT, s, assemble_kernel<double, true><<<nbk, kThreads, 0, s>>>(e0, e1, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats,
-                                                                 state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
-                                                                 h.d_slot, (double*)vals, residual, h.d_err));
-    } else {
-      FSI_LAUNCH(fsi::KC_RESIDUAL, s, assemble_kernel<double, false><<<nbk, kThreads, 0, s>>>(e0, e1, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats,
-                                                                state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
-                                                                h.d_slot, (double*)nullptr, residual, h.d_err));
+    if (want_tangent && f32) {
+      FSI_LAUNCH(fsi::KC_TANGENT, s, assemble_kernel<float, float, true><<<nbk, kThreads, 0, s>>>(
+          e0, e1, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef,
+          h.opts.fibre_factor, h.d_slot, (float*)vals, (double*)nullptr, h.d_err));
+    } else if (want_tangent) {
+      FSI_LAUNCH(fsi::KC_TANGENT, s, assemble_kernel<double, double, true><<<nbk, kThreads, 0, s>>>(
+          e0, e1, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef,
+          h.opts.fibre_factor, h.d_slot, (double*)vals, residual, h.d_err));
+    }
+    if ((!want_tangent || split) && residual) {
+      FSI_LAUNCH(fsi::KC_RESIDUAL, s, assemble_kernel<double, double, false><<<nbk, kThreads, 0, s>>>(
+          e0, e1, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef,
+          h.opts.fibre_factor, h.d_slot, (double*)nullptr, residual, h.d_err));
     }
   }
   FSI_CUDA_TRY(cudaGetLastError());

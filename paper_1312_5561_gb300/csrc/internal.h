@@ -158,6 +158,11 @@ struct Handle {
   int32_t* d_nf_ptr = nullptr;   // [n_nodes+1] node -> (face, local vertex) incidence
   int32_t* d_nf_idx = nullptr;   // [3 n_faces]: 3 * face + local vertex
   int32_t* d_seg_node = nullptr; // [n_nodes]
+  std::vector<int32_t> seg_ptr_host;  // [n_seg+1] node ranges of the segments
+  int32_t* d_seg_ptr = nullptr;
+  double* d_seg_a = nullptr;     // [n_seg] per-segment scratch
+  double* d_seg_b = nullptr;
+  double* h_seg = nullptr;       // pinned [n_seg]
   int* d_err = nullptr;          // device error word (bit 0 inverted, bit 1 bounds)
 
   // AMG hierarchy (level 0 = assembled matrix)
@@ -221,6 +226,10 @@ void scale_copy(double a, const double* x, double* y, long n, cudaStream_t s);
 void to_float(const double* x, float* y, long n, cudaStream_t s);
 void to_double(const float* x, double* y, long n, cudaStream_t s);
 void mask_vector(const uint8_t* cmask, double* x, long n, cudaStream_t s);
+// independent segments (batched meshes)
+void segment_sumsq(const int32_t* seg_ptr, int n_seg, const double* x, double* out, cudaStream_t s);
+void segment_normalise(int n_seg, double* a, double* b, cudaStream_t s);
+void segment_scale(const int32_t* seg_node, const double* scale, double* x, long n, cudaStream_t s);
 
 }  // namespace fsi
 

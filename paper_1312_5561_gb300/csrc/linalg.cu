@@ -98,6 +98,63 @@ __global__ void bsr_kernel(int n, const int32_t* __restrict__ row_ptr, const int
   }
 }
 
+// Block-row kernel for 7-row blocks (coarse levels, restriction): one warp
+// per block row.  Lane (j, r) = (lane / 7, lane % 7), j < 4: slot j takes
+// every fourth block of the row and row r of each; the four slot sums are
+// then added in a fixed order ((s0 + s2) + (s1 + s3)).  Long coarse rows
+// (~50 blocks) thereby keep 28 lanes busy instead of 7.  Modes as above.
+template <typename TV, typename TX, typename TA, int C, int MODE>
+__global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                            const TV* __restrict__ vals, const TX* __restrict__ x, const TX* __restrict__ b,
+                            const TV* __restrict__ dinv, TA omega, TX* __restrict__ y) {
+  constexpr int R = 7;
+  const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int j = lane / R, r = lane % R;
+  TA acc = 0;
+  if (row < n && lane < 4 * R) {
+    const int k1 = row_ptr[row + 1];
+    for (int k = row_ptr[row] + j; k < k1; k += 4) {
+      const TV* a = vals + (size_t)k * (R * C) + r * C;
+      const TX* xv = x + (size_t)col_idx[k] * C;
+      if constexpr (C == 4) {
+        TV v[4];
+        TX xx[4];
+        Vec4<TV>::load(a, v);
+        Vec4<TX>::load(xv, xx);
+        acc += (TA)v[0] * (TA)xx[0] + (TA)v[1] * (TA)xx[1] + (TA)v[2] * (TA)xx[2] + (TA)v[3] * (TA)xx[3];
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc += (TA)a[c] * (TA)xv[c];
+      }
+    }
+  }
+  acc += __shfl_down_sync(0xffffffffu, acc, 2 * R);
+  acc += __shfl_down_sync(0xffffffffu, acc, R);
+  const bool out = row < n && lane < R;
+  const size_t o = (size_t)row * R + lane;
+  if constexpr (MODE == 0) {
+    if (out) y[o] = (TX)acc;
+  } else if constexpr (MODE == 1) {
+    if (out) y[o] = (TX)((TA)b[o] - acc);
+  } else if constexpr (MODE == 3) {
+    if (out) y[o] = (TX)((TA)y[o] + acc);
+  } else {
+    static_assert(C == R, "Jacobi sweep needs square blocks");
+    const TA res = out ? (TA)b[o] - acc : (TA)0;
+    TA rr[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) rr[c] = __shfl_sync(0xffffffffu, res, c);
+    if (out) {
+      const TV* d = dinv + (size_t)row * (R * R) + lane * R;
+      TA corr = 0;
+#pragma unroll
+      for (int c = 0; c < R; ++c) corr += (TA)d[c] * rr[c];
+      y[o] = (TX)((TA)x[o] + omega * corr);
+    }
+  }
+}
+
 // x = omega D^-1 b (first Jacobi sweep from a zero guess), B x B blocks
 template <typename T, int B>
 __global__ void jacobi_zero_kernel(int n, const T* __restrict__ dinv, const T* __restrict__ b, T omega,
@@ -439,6 +496,32 @@ __global__ void mask_vector_kernel(const uint8_t* __restrict__ cmask, double* __
     if (cmask[t]) x[t] = 0.0;
 }
 
+// out[s] = sum of squares over the unknowns of segment s (nodes seg_ptr[s]..seg_ptr[s+1])
+__global__ void segment_sumsq_kernel(const int32_t* __restrict__ seg_ptr, const double* __restrict__ x,
+                                     double* __restrict__ out) {
+  const int sg = blockIdx.x;
+  const long d0 = 4L * seg_ptr[sg], d1 = 4L * seg_ptr[sg + 1];
+  double acc = 0.0;
+  for (long t = d0 + threadIdx.x; t < d1; t += blockDim.x) acc += x[t] * x[t];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[sg] = acc;
+}
+
+// mode 0: a[s] = 1/sqrt(sumsq) (1 if zero), b[s] = sqrt(sumsq); x *= a[seg]  (normalise)
+__global__ void segment_normalise_kernel(int n_seg, double* __restrict__ a, double* __restrict__ b) {
+  const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sg >= n_seg) return;
+  const double s = sqrt(a[sg]);
+  b[sg] = s > 0.0 ? s : 1.0;
+  a[sg] = s > 0.0 ? 1.0 / s : 1.0;
+}
+
+__global__ void segment_scale_kernel(const int32_t* __restrict__ seg_node, const double* __restrict__ scale,
+                                     double* __restrict__ x, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    x[t] *= scale[seg_node[t >> 2]];
+}
+
 inline int grid_stride_blocks(long n) {
   long b = (n + 255) / 256;
   return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
@@ -450,6 +533,12 @@ inline int grid_stride_blocks(long n) {
 template <typename TV, typename TX, typename TA, int R, int C, int MODE>
 static void bsr_launch(int n, const int32_t* rp, const int32_t* ci, const void* vals, const TX* x, const TX* b,
                        const void* dinv, TA omega, TX* y, cudaStream_t s, int cls) {
+  if constexpr (R == 7) {
+    if (n == 0) return;
+    FSI_LAUNCH(cls, s, bsr7_kernel<TV, TX, TA, C, MODE><<<blocks_for((long)n * 32, 128), 128, 0, s>>>(
+        n, rp, ci, (const TV*)vals, x, b, (const TV*)dinv, omega, y));
+    return;
+  }
   constexpr int LN = Lanes<R>::v;
   const long threads = (long)n * LN;
   if (threads == 0) return;
@@ -586,7 +675,9 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
     return;
   }
   Level& Lc = h.levels[level + 1];
-  smooth<T>(L, omega, h.opts.nu_pre, true, s);
+  const int nu_pre = level == 0 ? h.opts.nu_pre : h.opts.nu_coarse;
+  const int nu_post = level == 0 ? h.opts.nu_post : h.opts.nu_coarse;
+  smooth<T>(L, omega, nu_pre, true, s);
   if (L.bs == 4) {
     bsr_launch<T, T, T, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
                                  (T*)L.r, s, fsi::KC_BSR0);
@@ -601,7 +692,7 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
     bsr_launch<T, T, T, 4, 7, 3>(L.n, L.p_rp, L.p_ci, L.p_v, (const T*)Lc.x, nullptr, nullptr, T(0), (T*)L.x, s, fsi::KC_TRANSFER);
   else
     bsr_launch<T, T, T, 7, 7, 3>(L.n, L.p_rp, L.p_ci, L.p_v, (const T*)Lc.x, nullptr, nullptr, T(0), (T*)L.x, s, fsi::KC_TRANSFER);
-  smooth<T>(L, omega, h.opts.nu_post, false, s);
+  smooth<T>(L, omega, nu_post, false, s);
   FSI_CUDA_TRY(cudaGetLastError());
 }
 template void vcycle<double>(Handle&, int, cudaStream_t);
@@ -636,6 +727,21 @@ void to_float(const double* x, float* y, long n, cudaStream_t s) {
 
 void to_double(const float* x, double* y, long n, cudaStream_t s) {
   FSI_LAUNCH(fsi::KC_VECTOR, s, to_double_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, y, n));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void segment_sumsq(const int32_t* seg_ptr, int n_seg, const double* x, double* out, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, segment_sumsq_kernel<<<n_seg, kRedThreads, 0, s>>>(seg_ptr, x, out));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void segment_normalise(int n_seg, double* a, double* b, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, segment_normalise_kernel<<<blocks_for(n_seg, 128), 128, 0, s>>>(n_seg, a, b));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void segment_scale(const int32_t* seg_node, const double* scale, double* x, long n, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, segment_scale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(seg_node, scale, x, n));
   FSI_CUDA_TRY(cudaGetLastError());
 }
 

@@ -453,6 +453,9 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
   for (int i = 1; i < nn; ++i)
     if (comp[i] < comp[i - 1]) throw ArgError("seg_node must be non-decreasing (segments contiguous)");
   h.n_seg = nn ? comp[nn - 1] + 1 : 1;
+  h.seg_ptr_host.assign(h.n_seg + 1, 0);
+  for (int i = 0; i < nn; ++i) h.seg_ptr_host[comp[i] + 1]++;
+  for (int q = 0; q < h.n_seg; ++q) h.seg_ptr_host[q + 1] += h.seg_ptr_host[q];
 
   h.d_conn = upload(conn, s);
   h.d_slot = upload(slot, s);
@@ -466,6 +469,10 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
   h.d_nf_ptr = upload(nfp, s);
   h.d_nf_idx = upload(nfi, s);
   h.d_seg_node = upload(comp, s);
+  h.d_seg_ptr = upload(h.seg_ptr_host, s);
+  h.d_seg_a = dalloc<double>(h.n_seg);
+  h.d_seg_b = dalloc<double>(h.n_seg);
+  FSI_CUDA_TRY(cudaMallocHost((void**)&h.h_seg, sizeof(double) * h.n_seg));
   h.d_err = dalloc<int>(1);
   FSI_CUDA_TRY(cudaMemsetAsync(h.d_err, 0, sizeof(int), s));
   h.d_geo = dalloc<double>(16 * (size_t)ne);
@@ -522,6 +529,10 @@ static void destroy_impl(Handle* hp) {
                   (void*)h.d_res})
     dfree(p);
   if (h.h_dots) cudaFreeHost(h.h_dots);
+  if (h.h_seg) cudaFreeHost(h.h_seg);
+  dfree(h.d_seg_ptr);
+  dfree(h.d_seg_a);
+  dfree(h.d_seg_b);
   for (cudaEvent_t e : h.prof.pool) cudaEventDestroy(e);
   if (h.stream) cudaStreamDestroy(h.stream);
   delete hp;
@@ -547,8 +558,18 @@ static int newton_iterate(Handle& h, double* state, const fsi_load* load, double
   if (e & 8) throw CudaError("singular coarsest-level operator");
   scale_copy(-1.0, h.d_res, h.d_t, n, s);
   FSI_CUDA_TRY(cudaMemsetAsync(h.d_t2, 0, sizeof(double) * n, s));
+  // independent segments: solve with every segment's right-hand side scaled to
+  // unit norm (exact, the system is block diagonal), so that each segment is
+  // reduced by eps1 relative to its own residual
+  const bool segs = h.n_seg > 1;
+  if (segs) {
+    segment_sumsq(h.d_seg_ptr, h.n_seg, h.d_t, h.d_seg_a, s);
+    segment_normalise(h.n_seg, h.d_seg_a, h.d_seg_b, s);
+    segment_scale(h.d_seg_node, h.d_seg_a, h.d_t, n, s);
+  }
   double rel = 0.0;
   int its = linear_solve(h, h.d_t, h.d_t2, eps1, &rel, s);
+  if (segs) segment_scale(h.d_seg_node, h.d_seg_b, h.d_t2, n, s);
   axpy(1.0, h.d_t2, state, n, s);
   if (info) {
     info->krylov_its_total += its;
@@ -559,6 +580,15 @@ static int newton_iterate(Handle& h, double* state, const fsi_load* load, double
   (void)rn;
   if (rel > h.opts.krylov_rtol * 1e3 && its >= h.opts.max_krylov) return FSI_ERR_NOT_CONVERGED;
   return FSI_OK;
+}
+
+// per-segment residual norms (host copy)
+static void segment_norms(Handle& h, const double* x, std::vector<double>& out, cudaStream_t s) {
+  segment_sumsq(h.d_seg_ptr, h.n_seg, x, h.d_seg_a, s);
+  FSI_CUDA_TRY(cudaMemcpyAsync(h.h_seg, h.d_seg_a, sizeof(double) * h.n_seg, cudaMemcpyDeviceToHost, s));
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  out.resize(h.n_seg);
+  for (int q = 0; q < h.n_seg; ++q) out[q] = std::sqrt(h.h_seg[q]);
 }
 
 static int solve_impl(Handle& h, double* state, const fsi_load* load, const double* guess, fsi_info* info,
@@ -591,9 +621,18 @@ static int solve_impl(Handle& h, double* state, const fsi_load* load, const doub
     }
   }
   double eps_prev = 1.0;
+  std::vector<double> seg0, segk;
+  if (h.n_seg > 1) segment_norms(h, h.d_res, seg0, s);
+  auto converged = [&]() {
+    if (h.n_seg == 1) return r0 == 0.0 || rn <= h.opts.newton_rtol * r0;
+    segment_norms(h, h.d_res, segk, s);
+    for (int q = 0; q < h.n_seg; ++q)
+      if (segk[q] > h.opts.newton_rtol * seg0[q]) return false;
+    return true;
+  };
   int k = 0;
   for (;; ++k) {
-    if (r0 == 0.0 || rn <= h.opts.newton_rtol * r0) break;
+    if (converged()) break;
     if (k >= h.opts.max_newton) {
       info->newton_its = k;
       info->res = rn;
@@ -666,8 +705,9 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->max_krylov = 300;
   o->max_newton = 25;
   o->smoother = FSI_SMOOTHER_JACOBI;
-  o->nu_pre = 3;
-  o->nu_post = 3;
+  o->nu_pre = 4;
+  o->nu_post = 4;
+  o->nu_coarse = 1;
   o->cheb_degree = 3;
   o->coarse_max_nodes = 16;
   o->max_levels = 12;

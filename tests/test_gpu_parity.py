@@ -225,3 +225,57 @@ def test_fp32_refinement_reaches_fp64_solution():
     ref = _oracle_ramp(mesh, 2, pressure=0.32)
     got = state.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- batched independent segments
+def test_batched_segments_match_oracle():
+    """Uneven artery segments (own angles, kappa, pressure) in one handle: each
+    segment converges to the oracle solution of the union mesh."""
+    from fixtures import batched_tubes
+    from paper_1312_5561_gb300.binding import Load
+    mesh = batched_tubes(n_seg=3, seed=7, ne_range=(2.0e3, 7.0e3))
+    solver = _solver(mesh, precision=1, newton_rtol=1e-10, krylov_rtol=1e-8, max_krylov=600)
+    assert solver.levels()[-1][0] >= 3            # the coarsest level keeps one block per segment at least
+    fp = _t(mesh.face_pressure)
+    state = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
+    for k in (1, 2):
+        info = solver.solve(state, Load(pressure=0.1 * k, face_pressure=fp))
+        assert info.status == 0
+    got = state.cpu().numpy()
+    for sg in range(3):
+        sub = _segment(mesh, sg)
+        P = O.Problem(sub)
+        ref = np.zeros((sub.n_nodes, 4))
+        for k in (1, 2):
+            ref, _ = P.newton(ref, fext=P.external_force(0.1 * k, face_pressure=sub.face_pressure), rtol=1e-12)
+        m = mesh.seg_node == sg
+        assert np.abs(got[m] - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def _segment(mesh, sg):
+    """Segment sg of a batched mesh as a mesh of its own (nodes keep their order)."""
+    from fixtures.meshes import Mesh
+    nodes = np.flatnonzero(mesh.seg_node == sg)
+    off = nodes[0]
+    em = mesh.seg_elem == sg
+    fm = mesh.seg_face == sg
+    mats = mesh.materials[2 * sg:2 * sg + 2]
+    return Mesh(X=mesh.X[nodes], tets=(mesh.tets[em] - off).astype(np.int32), mat_id=mesh.mat_id[em] - 2 * sg,
+                fibre=mesh.fibre[em], dir_mask=mesh.dir_mask[nodes], neu_faces=(mesh.neu_faces[fm] - off).astype(np.int32),
+                materials=mats, face_pressure=mesh.face_pressure[fm])
+
+
+def test_adaptive_inner_tolerance_keeps_the_solution():
+    """eps_1,k = eps_2,k-1^2 (Sec. 4.4): fewer Krylov iterations, same Newton solution."""
+    from paper_1312_5561_gb300.binding import Load
+    mesh = artery_tube(n_theta=64, n_z=8, length=0.5, materials=artery_layers(1.0e3))
+    its = {}
+    sols = {}
+    for adaptive in (0, 1):
+        solver = _solver(mesh, newton_rtol=1e-10, krylov_rtol=1e-10, adaptive_tol=adaptive, max_krylov=600)
+        state = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
+        info = solver.solve(state, Load(pressure=0.16))
+        its[adaptive] = info.krylov_its_total
+        sols[adaptive] = state.cpu().numpy()
+    assert its[1] < its[0]
+    assert np.abs(sols[1] - sols[0]).max() <= 1e-8 * np.abs(sols[0]).max()
