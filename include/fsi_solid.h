@@ -223,6 +223,28 @@ int64_t fsi_solid_launch_count(void);
  * stops it.  Either output pointer may be NULL. */
 fsi_status fsi_solid_kernel_timing(fsi_solid_t h, int32_t enable, double* ms_out, int64_t* launches_out);
 
+/* Allocation-free dot products: out[i] = V_i . y for V_i = V + i * ldv,
+ * i < k (device FP64 arrays; out is device memory of k doubles).  The paper
+ * has no counterpart: this call is for callers that cannot allocate device
+ * memory -- a coupling driver or host application that owns every device
+ * allocation and hands this library only fixed buffers, or code that may not
+ * call cudaMalloc / cudaFree after start-up because those calls synchronise
+ * the device and stall its other streams.  It needs no handle and allocates
+ * nothing: its partial sums live in a fixed file-scope device array of
+ * FSI_DOTS_STATIC_MAX_VECTORS x 256 doubles (64 KiB) that every GPU which
+ * loads the library keeps until the process exits.  k must lie in
+ * [1, FSI_DOTS_STATIC_MAX_VECTORS] (FSI_ERR_ARG otherwise) and ldv >= n when
+ * k > 1.  The sums use the same deterministic two-pass reduction as the
+ * solver (one partial per CTA, then a fixed-order sum), so repeated calls
+ * give identical results.  The first call on each device looks up the
+ * array's device address on that device (make that first call before any
+ * stream capture).  All calls share the one array: calls that overlap on the
+ * GPU (different streams or threads) race and must be serialised by the
+ * caller.  Returns after the work on `stream` has finished. */
+#define FSI_DOTS_STATIC_MAX_VECTORS 32
+fsi_status fsi_dots_static(const double* V, int64_t ldv, int32_t k, const double* y, int64_t n, double* out,
+                           void* stream);
+
 /* Description of the last error on this handle (static storage of the handle). */
 const char* fsi_solid_last_error(fsi_solid_t h);
 

@@ -27,7 +27,7 @@ EXPORTS = [
     "fsi_solid_default_opts", "fsi_solid_create", "fsi_solid_destroy", "fsi_solid_residual_tangent",
     "fsi_solid_get_bsr", "fsi_solid_spmv", "fsi_solid_linear_solve", "fsi_solid_newton_step",
     "fsi_solid_solve", "fsi_solid_get_colouring", "fsi_solid_get_levels", "fsi_solid_last_error",
-    "fsi_solid_launch_count", "fsi_solid_kernel_timing",
+    "fsi_solid_launch_count", "fsi_solid_kernel_timing", "fsi_dots_static",
 ]
 
 # kernel classes of fsi_solid_kernel_timing (FSI_KC_* in the header)
@@ -107,6 +107,8 @@ def _load_library():
     lib.fsi_solid_launch_count.restype = C.c_int64
     lib.fsi_solid_kernel_timing.argtypes = [vp, i32, vp, vp]
     lib.fsi_solid_kernel_timing.restype = i32
+    lib.fsi_dots_static.argtypes = [vp, C.c_int64, i32, vp, C.c_int64, vp, vp]
+    lib.fsi_dots_static.restype = i32
     return lib
 
 

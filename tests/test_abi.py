@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "fsi_solid.h")).read()
-    return sorted(set(re.findall(r"\b(fsi_solid_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(fsi_[a-z_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
