@@ -49,8 +49,10 @@ def _peaks():
     return PEAKS_FALLBACK, "fallback"
 
 
-def workload_mesh(nz=128):
-    from fixtures import artery_layers, artery_tube
+def workload_mesh(nz=128, config="tube", nseg=256):
+    from fixtures import artery_layers, artery_tube, batched_tubes
+    if config == "batched":
+        return batched_tubes(n_seg=nseg, seed=4)
     return artery_tube(n_theta=64, n_media=4, n_adv=4, n_z=nz, length=8.0 * nz / 128,
                        materials=artery_layers(1.0e3))
 
@@ -109,9 +111,10 @@ def jacobi0_bytes(n, nb, fp32):
 class RampDriver:
     """Advances the pressure ramp between Newton steps."""
 
-    def __init__(self, solver, n, torch):
+    def __init__(self, solver, n, torch, face_pressure=None):
         from paper_1312_5561_gb300.binding import Load
         self.Load = Load
+        self.fp = None if face_pressure is None else torch.tensor(face_pressure, device="cuda", dtype=torch.float64)
         self.solver = solver
         self.torch = torch
         self.state = torch.zeros((n, 4), device="cuda", dtype=torch.float64)
@@ -121,7 +124,8 @@ class RampDriver:
 
     def step(self, state=None):
         st = self.state if state is None else state
-        info = self.solver.newton_step(st, self.Load(pressure=P_MAX * self.k / N_LOADS), check=False)
+        scale = (P_MAX if self.fp is None else 1.0) * self.k / N_LOADS
+        info = self.solver.newton_step(st, self.Load(pressure=scale, face_pressure=self.fp), check=False)
         if info.status not in (0, -5):
             raise RuntimeError(f"newton_step failed with status {info.status}")
         if self.r0 is None:
@@ -141,17 +145,19 @@ def run_gpu(args, rank, world):
     import torch
     from paper_1312_5561_gb300.binding import SolidSolver, launch_count
     torch.cuda.set_device(args.local_rank)
-    mesh = workload_mesh(args.nz)
+    mesh = workload_mesh(args.nz, args.config, args.nseg)
     prec = 1 if args.precision == "fp32" else 0
-    solver = SolidSolver(mesh, precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, max_krylov=600)
+    t_create = time.perf_counter()
+    solver = SolidSolver(mesh, precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, max_krylov=600,
+                         use_graphs=int(args.graphs))
+    t_create = time.perf_counter() - t_create
     levels = solver.levels()
-    drv = RampDriver(solver, mesh.n_nodes, torch)
+    drv = RampDriver(solver, mesh.n_nodes, torch, getattr(mesh, "face_pressure", None))
     for _ in range(args.warmup):
         drv.step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    solver.kernel_timing(True)
     l0 = launch_count()
     clocks = ClockSampler(args.local_rank)
     clocks.start()
@@ -168,6 +174,13 @@ def run_gpu(args, rank, world):
     clk = clocks.stop()
     launches = launch_count() - l0
     ms_total = ev0.elapsed_time(ev1)
+    # kernel-timing pass: the same Newton steps continued, with CUDA events recorded
+    # on the launching stream around every launch (the V-cycle is then launched
+    # kernel by kernel instead of from its graph)
+    solver.kernel_timing(True)
+    for _ in range(args.prof_steps):
+        drv.step()
+    torch.cuda.synchronize()
     prof = solver.kernel_timing(False)
     if world > 1:
         t = torch.tensor([ms_total], device="cuda")
@@ -216,13 +229,15 @@ def run_gpu(args, rank, world):
         roof = {"kernel": "bsr_kernel<...,4,4,MODE=2> (finest-level block-Jacobi sweep)", "bound": "hbm",
                 "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / peaks["hbm_gbs"], 3), "traffic": None, "peak_source": src,
-                "bytes_per_launch": int(byt), "avg_launch_us": round(per_launch_s * 1e6, 2)}
+                "bytes_per_launch": int(byt), "avg_launch_us": round(per_launch_s * 1e6, 2),
+                "timing": f"CUDA events around each launch over a {args.prof_steps}-step kernel-timing pass "
+                          f"following the timed region (same workload, V-cycle launched eagerly)"}
     return {
         "steps_per_s": steps_per_s, "ms_per_step": ms_total / args.steps, "tangents_per_s": tangents_per_s,
         "e2e_steps_per_s": e2e, "bytes": nbytes, "launches": launches, "clocks": clk,
         "prof": {k: [round(v[0], 3), v[1]] for k, v in prof.items()}, "dominant": dominant, "roofline": roof,
         "krylov_per_step": krylov / args.steps, "levels": levels, "n_elems": mesh.n_elems,
-        "n_nodes": mesh.n_nodes,
+        "n_nodes": mesh.n_nodes, "create_s": t_create,
     }
 
 
@@ -284,16 +299,24 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--nz", type=int, default=128)
+    ap.add_argument("--config", default="tube", choices=["tube", "batched"])
+    ap.add_argument("--nseg", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single", action="store_true", help="skip the plain-FP64 comparison run")
+    ap.add_argument("--graphs", type=int, default=1, help="replay the V-cycle from a captured CUDA graph")
+    ap.add_argument("--prof-steps", type=int, default=6, help="Newton steps of the kernel-timing pass")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     args.local_rank = int(os.environ.get("LOCAL_RANK", 0))
     full_elems = 64 * 8 * args.nz * 6
-    config = {"workload": f"two-layer artery tube 64x8x{args.nz} hex x6 tets ({full_elems} tets), kappa=1e3*c10, "
-                          f"pressure ramp 0->1.6 in 10 load steps", "mesh_elems": full_elems,
+    wl = (f"two-layer artery tube 64x8x{args.nz} hex x6 tets ({full_elems} tets), kappa=1e3*c10, "
+          f"pressure ramp 0->1.6 in 10 load steps")
+    if args.config == "batched":
+        wl = (f"{args.nseg} independent artery segments in one handle (seed 4): n_e logU[5e3,2e5], angles U[20,70], "
+              f"kappa/c10 logU[1e2,1e5], pressure U[0.5,2.0] ramped in 10 load steps")
+    config = {"workload": wl, "mesh_elems": full_elems,
               "l2": "inputs larger than L2 (matrix + AMG hierarchy + Krylov basis ~1 GB)", "parallelism": "replicas"}
 
     if args.impl == "reference":
@@ -336,7 +359,11 @@ def main():
                 "h2d_bytes_per_step": res["bytes"], "d2h_bytes_per_step": res["bytes"]},
         "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": res["roofline"],
         "kernel_ms": res["prof"], "dominant_kernel_class": res["dominant"],
+        "create_s": round(res["create_s"], 2),
     }
+    if args.config == "batched":
+        out["config"]["mesh_elems"] = res["n_elems"]
+        out["segment_newton_steps_per_s"] = value * args.nseg
     if other is not None:
         out["plain_fp64"] = {"value": other["steps_per_s"] * world, "ms_per_step": other["ms_per_step"],
                              "element_tangents_per_s": other["tangents_per_s"] * world,

@@ -105,6 +105,11 @@ typedef struct {
   double krylov_rtol;       /* relative residual reduction of each linear solve */
   double fibre_factor;      /* 2: S = 2 dPsi/dC; 1: the factor printed in Eq. arpkt */
   double inertia_coef;      /* 1/(beta dt^2) of the Newmark-beta scheme; 0 = quasi-static */
+  int32_t amg_lag;          /* recompute the coarse AMG levels on every (amg_lag+1)-th
+                               Newton step only (0: every step); the finest level is
+                               always the current tangent */
+  int32_t assembly;         /* 0: element buffers + fixed-order gather (default);
+                               1: colour-ordered scatter; both bit-reproducible */
 } fsi_solver_opts;
 
 /* Load of one solve (device arrays owned by the caller; NULL = absent).
@@ -138,7 +143,8 @@ typedef struct {
 } fsi_info;
 
 /* Default options: FP64, FGMRES(100), block Jacobi 4+4 sweeps on the finest
- * level and 1+1 on coarser levels, omega 0.7,
+ * level and 1+1 on coarser levels, omega 0.7, V-cycle replayed from a CUDA
+ * graph, coarse levels refreshed every Newton step,
  * Newton rtol 1e-8, Krylov rtol 1e-8, PSPG on, fibre_factor 2. */
 void fsi_solid_default_opts(fsi_solver_opts* opts);
 
@@ -188,6 +194,15 @@ fsi_status fsi_solid_newton_step(fsi_solid_t h, double* state, const fsi_load* l
 fsi_status fsi_solid_solve(fsi_solid_t h, double* state, const fsi_load* load, const double* guess,
                            fsi_info* info, void* stream);
 
+/* Newmark-beta update after the solve of time step n (Sec. 4.1.2):
+ *   a_n = (d_n - d_(n-1)) / (beta dt^2) - v_(n-1) / (beta dt) - (1 - 2 beta)/(2 beta) a_(n-1)
+ *   v_n = v_(n-1) + dt ((1 - gamma) a_(n-1) + gamma a_n)
+ * and the history of the next step h = d_n/(beta dt^2) + v_n/(beta dt) + (1-2beta)/(2beta) a_n
+ * (r_s = rho h, see fsi_load.hist).  state: device [n][4] (d_n in columns 0..2);
+ * disp [n][3] holds d_(n-1) on entry and d_n on return; vel, acc, hist [n][3]. */
+fsi_status fsi_solid_newmark_advance(fsi_solid_t h, const double* state, double* disp, double* vel, double* acc,
+                                     double* hist, double beta, double gamma, double dt, void* stream);
+
 /* Host copy of the element colouring in original element order
  * (colour_out [n_elems]); returns the number of colours in *n_colours. */
 fsi_status fsi_solid_get_colouring(fsi_solid_t h, int32_t* colour_out, int32_t* n_colours);
@@ -220,8 +235,36 @@ int64_t fsi_solid_launch_count(void);
  * around each launch) and in launches_out[FSI_KC_COUNT] the launch counts
  * accumulated since the previous call, then resets them; enable = 1 keeps
  * (or starts) recording for the following calls on this handle, enable = 0
- * stops it.  Either output pointer may be NULL. */
+ * stops it.  While recording, the V-cycle is launched kernel by kernel
+ * instead of from its CUDA graph.  Either output pointer may be NULL. */
 fsi_status fsi_solid_kernel_timing(fsi_solid_t h, int32_t enable, double* ms_out, int64_t* launches_out);
+
+/* ------------------------------------------------------------------------
+ * Learned Newton initial guess (a per-node MLP; the paper has no counterpart:
+ * Newton itself, unchanged, corrects whatever the network proposes and the
+ * zero increment remains the fallback, see fsi_solid_solve's guess).
+ * Layers l = 0..n_layers-1 map sizes[l] -> sizes[l+1]; hidden layers use
+ * tanh, the last is affine.  Parameters are FP32, laid out per layer as
+ * W_l [sizes[l+1]][sizes[l]] then b_l [sizes[l+1]].  Training minimises
+ * L = 1/(2N) sum_n sum_o w_o (Y_no - T_no)^2 with Adam (b1 0.9, b2 0.999,
+ * eps 1e-8).  Device arrays: X [n][sizes[0]], T and Y [n][sizes[L]], FP32. */
+typedef struct fsi_mlp_s* fsi_mlp_t;
+
+/* Create a network; weights U(-a, a), a = sqrt(6/(fan_in + fan_out)), from a
+ * splitmix64 stream seeded by `seed`; biases zero. */
+fsi_status fsi_mlp_create(int32_t n_layers, const int32_t* sizes, uint64_t seed, fsi_mlp_t* out);
+fsi_status fsi_mlp_destroy(fsi_mlp_t h);
+int64_t fsi_mlp_num_params(fsi_mlp_t h);
+/* Copy the parameters to (set = 0) or from (set = 1) the host array `host`. */
+fsi_status fsi_mlp_params(fsi_mlp_t h, float* host, int32_t set);
+/* Y = net(X); bf16 = 1 runs every layer on the tensor cores in BF16 with FP32
+ * accumulation (every sizes[l] < sizes[L] must then be a multiple of 16). */
+fsi_status fsi_mlp_forward(fsi_mlp_t h, const float* X, int32_t n, float* Y, int32_t bf16, void* stream);
+/* Forward + backward on one batch; loss_out (host, may be NULL) gets L,
+ * grad_host (host, may be NULL) the gradient; apply = 1 then takes one Adam
+ * step with learning rate lr.  w_out: device [sizes[L]] output weights or NULL. */
+fsi_status fsi_mlp_train_step(fsi_mlp_t h, const float* X, const float* T, int32_t n, const float* w_out, float lr,
+                              int32_t apply, float* loss_out, float* grad_host, void* stream);
 
 /* Allocation-free dot products: out[i] = V_i . y for V_i = V + i * ldv,
  * i < k (device FP64 arrays; out is device memory of k doubles).  The paper

@@ -28,6 +28,8 @@ EXPORTS = [
     "fsi_solid_get_bsr", "fsi_solid_spmv", "fsi_solid_linear_solve", "fsi_solid_newton_step",
     "fsi_solid_solve", "fsi_solid_get_colouring", "fsi_solid_get_levels", "fsi_solid_last_error",
     "fsi_solid_launch_count", "fsi_solid_kernel_timing", "fsi_dots_static",
+    "fsi_mlp_create", "fsi_mlp_destroy", "fsi_mlp_num_params", "fsi_mlp_params", "fsi_mlp_forward",
+    "fsi_mlp_train_step", "fsi_solid_newmark_advance",
 ]
 
 # kernel classes of fsi_solid_kernel_timing (FSI_KC_* in the header)
@@ -54,7 +56,8 @@ class SolverOpts(C.Structure):
                 ("coarse_max_nodes", C.c_int32), ("max_levels", C.c_int32), ("use_pspg", C.c_int32),
                 ("adaptive_tol", C.c_int32), ("use_graphs", C.c_int32), ("nu_coarse", C.c_int32),
                 ("omega", C.c_double), ("newton_rtol", C.c_double), ("krylov_rtol", C.c_double),
-                ("fibre_factor", C.c_double), ("inertia_coef", C.c_double)]
+                ("fibre_factor", C.c_double), ("inertia_coef", C.c_double), ("amg_lag", C.c_int32),
+                ("assembly", C.c_int32)]
 
 
 class LoadDesc(C.Structure):
@@ -109,6 +112,20 @@ def _load_library():
     lib.fsi_solid_kernel_timing.restype = i32
     lib.fsi_dots_static.argtypes = [vp, C.c_int64, i32, vp, C.c_int64, vp, vp]
     lib.fsi_dots_static.restype = i32
+    lib.fsi_mlp_create.argtypes = [i32, vp, C.c_uint64, C.POINTER(vp)]
+    lib.fsi_mlp_create.restype = i32
+    lib.fsi_mlp_destroy.argtypes = [vp]
+    lib.fsi_mlp_destroy.restype = i32
+    lib.fsi_mlp_num_params.argtypes = [vp]
+    lib.fsi_mlp_num_params.restype = C.c_int64
+    lib.fsi_mlp_params.argtypes = [vp, vp, i32]
+    lib.fsi_mlp_params.restype = i32
+    lib.fsi_mlp_forward.argtypes = [vp, vp, i32, vp, i32, vp]
+    lib.fsi_mlp_forward.restype = i32
+    lib.fsi_mlp_train_step.argtypes = [vp, vp, vp, i32, vp, C.c_float, i32, vp, vp, vp]
+    lib.fsi_mlp_train_step.restype = i32
+    lib.fsi_solid_newmark_advance.argtypes = [vp, vp, vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, vp]
+    lib.fsi_solid_newmark_advance.restype = i32
     return lib
 
 
@@ -279,6 +296,12 @@ class SolidSolver:
         self._check(lib.fsi_solid_get_colouring(self.h, out.ctypes.data, C.byref(nc)))
         return out, nc.value
 
+    def newmark_advance(self, state, disp, vel, acc, hist, beta, gamma, dt):
+        """Newmark-beta update after a converged step (see the header)."""
+        self._check(lib.fsi_solid_newmark_advance(self.h, _dev_ptr(state), _dev_ptr(disp), _dev_ptr(vel),
+                                                  _dev_ptr(acc), _dev_ptr(hist), float(beta), float(gamma),
+                                                  float(dt), _stream()))
+
     def kernel_timing(self, enable: bool):
         """Per-class device time (ms) and launch counts since the last call;
         ``enable`` switches event recording on or off for later calls."""
@@ -294,6 +317,69 @@ class SolidSolver:
         nl = C.c_int32()
         self._check(lib.fsi_solid_get_levels(self.h, nodes.ctypes.data, blocks.ctypes.data, cap, C.byref(nl)))
         return list(zip(nodes[:nl.value].tolist(), blocks[:nl.value].tolist()))
+
+
+def _f32_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float32 tensor")
+    return t.data_ptr()
+
+
+class Mlp:
+    """Per-node MLP of the learned initial guess (fsi_mlp_* in the header)."""
+
+    def __init__(self, sizes, seed=0):
+        self.sizes = [int(s) for s in sizes]
+        arr = np.asarray(self.sizes, dtype=np.int32)
+        h = C.c_void_p()
+        st = lib.fsi_mlp_create(len(self.sizes) - 1, arr.ctypes.data, int(seed), C.byref(h))
+        if st != FSI_OK:
+            raise FsiError(st, "fsi_mlp_create failed")
+        self.h = h
+        self.n_params = int(lib.fsi_mlp_num_params(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fsi_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        st = lib.fsi_mlp_params(self.h, out.ctypes.data, 0)
+        if st != FSI_OK:
+            raise FsiError(st, "fsi_mlp_params")
+        return out
+
+    def set_params(self, flat):
+        arr = np.ascontiguousarray(flat, dtype=np.float32)
+        st = lib.fsi_mlp_params(self.h, arr.ctypes.data, 1)
+        if st != FSI_OK:
+            raise FsiError(st, "fsi_mlp_params")
+
+    def forward(self, X, bf16=False):
+        import torch
+        Y = torch.empty((X.shape[0], self.sizes[-1]), device=X.device, dtype=torch.float32)
+        st = lib.fsi_mlp_forward(self.h, _f32_ptr(X), int(X.shape[0]), _f32_ptr(Y), int(bool(bf16)), _stream())
+        if st != FSI_OK:
+            raise FsiError(st, "fsi_mlp_forward")
+        return Y
+
+    def train_step(self, X, T, lr=1e-3, w_out=None, apply=True, want_grad=False):
+        loss = C.c_float()
+        grad = np.empty(self.n_params, np.float32) if want_grad else None
+        st = lib.fsi_mlp_train_step(self.h, _f32_ptr(X), _f32_ptr(T), int(X.shape[0]),
+                                    None if w_out is None else _f32_ptr(w_out), float(lr), int(bool(apply)),
+                                    C.byref(loss), None if grad is None else grad.ctypes.data, _stream())
+        if st != FSI_OK:
+            raise FsiError(st, "fsi_mlp_train_step")
+        return (loss.value, grad) if want_grad else loss.value
 
 
 def launch_count() -> int:

@@ -238,6 +238,18 @@ double power_lambda(const HostBsr& A, const std::vector<double>& Dinv, const std
   return lam;
 }
 
+// Copy of A without the couplings between displacement-like unknowns (the
+// first 3 of a 4-block, the first 6 of a 7-block) and pressure-like ones.
+HostBsr filter_up(const HostBsr& A) {
+  HostBsr F = A;
+  const int b = A.br, nu = (b == 4) ? 3 : 6;
+  for (int k = 0; k < F.nb(); ++k)
+    for (int r = 0; r < b; ++r)
+      for (int c = 0; c < b; ++c)
+        if ((r < nu) != (c < nu)) F.v[((size_t)k * b + r) * b + c] = 0.0;
+  return F;
+}
+
 void block_inverses(const HostBsr& A, std::vector<double>& Dinv) {
   const int b = A.br;
   Dinv.assign((size_t)A.n * b * b, 0.0);
@@ -255,7 +267,7 @@ void block_inverses(const HostBsr& A, std::vector<double>& Dinv) {
 }  // namespace
 
 void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
-                        const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap,
+                        const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap, bool filter,
                         std::vector<HostLevel>& levels, HostCoarse& coarse) {
   levels.clear();
   levels.emplace_back();
@@ -353,7 +365,17 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
     }
     // P pattern = pattern of A P_t; W plan: the A blocks of row i whose column
     // lies in aggregate J feed P block (i, J)
-    const double lam = power_lambda(A, L.Dinv, L.free);
+    // prolongator smoothing operator: A itself, or (filter) A without the
+    // displacement-pressure couplings
+    HostBsr Af;
+    std::vector<double> Dinv_f;
+    if (filter) {
+      Af = filter_up(A);
+      block_inverses(Af, Dinv_f);
+    }
+    const HostBsr& As = filter ? Af : A;
+    const std::vector<double>& Ds = filter ? Dinv_f : L.Dinv;
+    const double lam = power_lambda(As, Ds, L.free);
     const double wP = 4.0 / (3.0 * std::max(lam, 1e-300));
     const int pb = b * NS;
     HostBsr P;
@@ -387,10 +409,10 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
           std::fill(W.begin(), W.end(), 0.0);
           for (int s = w_ptr[q]; s < w_ptr[q + 1]; ++s) {
             const int k = w_k[s];
-            gemm_acc(&A.v[(size_t)k * b * b], &Pt.v[(size_t)A.ci[k] * pb], W.data(), b, b, NS);
+            gemm_acc(&As.v[(size_t)k * b * b], &Pt.v[(size_t)A.ci[k] * pb], W.data(), b, b, NS);
           }
           std::fill(tmp.begin(), tmp.end(), 0.0);
-          gemm_acc(&L.Dinv[(size_t)i * b * b], W.data(), tmp.data(), b, b, NS, -wP);
+          gemm_acc(&Ds[(size_t)i * b * b], W.data(), tmp.data(), b, b, NS, -wP);
           if (P.ci[q] == agg[i])
             for (int e = 0; e < pb; ++e) tmp[e] += Pt.v[(size_t)i * pb + e];
           for (int d = 0; d < b; ++d)

@@ -44,8 +44,11 @@ struct HostCoarse {
 
 // Builds levels[0..] from the level-0 matrix A0 (4x4 blocks), its free mask,
 // the node coordinates X [n][3] and components comp0 (non-decreasing).
+// filter: smooth the prolongator with A minus its displacement-pressure
+// couplings (needed when inertia dominates the displacement block: the PSPG
+// inertia coupling then blows up the pressure rows of D^-1 A).
 void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
-                        const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap,
+                        const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap, bool filter,
                         std::vector<HostLevel>& levels, HostCoarse& coarse);
 
 }  // namespace fsi

@@ -396,6 +396,100 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(
   }
 }
 
+// Gather-based assembly.  Every element writes its 16 residual entries and
+// 16 tangent blocks to a per-element buffer in one launch; the global
+// residual and BSR values are then formed by gathering, for each node and
+// each block, its contributions in a fixed order (deterministic without
+// colours or atomics, and every launch fills the GPU).
+template <typename T>
+struct BufEmit {
+  T* out;   // [16][16] of this element
+  template <typename TC>
+  __device__ __forceinline__ void operator()(int ab, const TC (&K)[4][4]) const {
+    T* v = out + 16 * ab;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[4 * r + c] = (T)K[r][c];
+  }
+};
+
+template <typename T, typename TC, bool TANGENT>
+__global__ void __launch_bounds__(kThreads) element_buffer_kernel(
+    int ne, const int32_t* __restrict__ conn, const double* __restrict__ geo, const double* __restrict__ fibre,
+    const int32_t* __restrict__ mat, const double* __restrict__ mats, const double* __restrict__ state,
+    const double* __restrict__ hist, double inertia, double fibre_factor, T* __restrict__ ek,
+    double* __restrict__ er, int* __restrict__ err) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  ElemIn in;
+  const double* ge = geo + 16 * (size_t)e;
+  for (int a = 0; a < 4; ++a) {
+    const int nid = conn[4 * e + a];
+    const double* s = state + 4 * (size_t)nid;
+    for (int i = 0; i < 3; ++i) {
+      in.u[a][i] = s[i];
+      in.g[a][i] = ge[3 * a + i];
+      in.hs[a][i] = hist ? hist[3 * (size_t)nid + i] : 0.0;
+    }
+    in.p[a] = s[3];
+  }
+  in.V = ge[12];
+  in.tauV = ge[13];
+  TC R[4][4];
+  BufEmit<T> emit{ek + 256 * (size_t)e};
+  if (!element_eval<TC, TANGENT>(in, mats + 8 * mat[e], fibre + 6 * (size_t)e, inertia, fibre_factor, R, emit)) {
+    atomicOr(err, 1);
+    if (er)
+      for (int q = 0; q < 16; ++q) er[16 * (size_t)e + q] = 0.0;
+    if (TANGENT)
+      for (int q = 0; q < 256; ++q) ek[256 * (size_t)e + q] = T(0);
+    return;
+  }
+  if (er)
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) er[16 * (size_t)e + 4 * a + c] = (double)R[a][c];
+}
+
+// vals[b][q] = sum over the contributions of block b (fixed order), with the
+// Dirichlet rows/columns replaced by identity rows and zero columns.
+template <typename T>
+__global__ void gather_tangent_kernel(int nb, const int32_t* __restrict__ bptr, const int32_t* __restrict__ bsrc,
+                                      const T* __restrict__ ek, const int32_t* __restrict__ block_row,
+                                      const int32_t* __restrict__ col_idx, const uint8_t* __restrict__ mask,
+                                      T* __restrict__ vals) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = (int)(t >> 4), q = (int)(t & 15);
+  if (b >= nb) return;
+  const int i = block_row[b], j = col_idx[b];
+  const int r = q >> 2, c = q & 3;
+  T v;
+  if (mask[4 * i + r] || mask[4 * j + c]) {
+    v = (i == j && r == c && mask[4 * i + r]) ? T(1) : T(0);
+  } else {
+    float accf = 0.f;
+    double accd = 0.0;
+    for (int k = bptr[b]; k < bptr[b + 1]; ++k) {
+      const T x = ek[16 * (size_t)bsrc[k] + q];
+      if (sizeof(T) == 4) accf += (float)x; else accd += (double)x;
+    }
+    v = (sizeof(T) == 4) ? (T)accf : (T)accd;
+  }
+  vals[16 * (size_t)b + q] = v;
+}
+
+// res[i][c] = sum over the element contributions of node i - f_ext, masked
+__global__ void gather_residual_kernel(int n, const int32_t* __restrict__ nptr, const int32_t* __restrict__ nsrc,
+                                       const double* __restrict__ er, const double* __restrict__ fext,
+                                       const uint8_t* __restrict__ mask, double* __restrict__ res) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * n) return;
+  const int i = t >> 2, c = t & 3;
+  double acc = (c < 3 && fext) ? -fext[3 * (size_t)i + c] : 0.0;
+  for (int k = nptr[i]; k < nptr[i + 1]; ++k) acc += er[4 * (size_t)nsrc[k] + c];
+  res[t] = mask[t] ? 0.0 : acc;
+}
+
 // R = -f_ext on displacement rows, 0 on pressure rows
 __global__ void init_residual_kernel(int n, const double* __restrict__ fext, double* __restrict__ res) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -469,7 +563,30 @@ __global__ void set_dirichlet_kernel(int n, const uint8_t* __restrict__ mask, co
 
 inline int blocks_for(long n, int t) { return (int)((n + t - 1) / t); }
 
+__global__ void newmark_kernel(int n, const double* __restrict__ state, double* __restrict__ disp,
+                               double* __restrict__ vel, double* __restrict__ acc, double* __restrict__ hist,
+                               double beta, double gamma, double dt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int i = t / 3, c = t % 3;
+  const double dn = state[4 * (size_t)i + c];
+  const double a_new = (dn - disp[t]) / (beta * dt * dt) - vel[t] / (beta * dt) -
+                       (1.0 - 2.0 * beta) / (2.0 * beta) * acc[t];
+  const double v_new = vel[t] + dt * ((1.0 - gamma) * acc[t] + gamma * a_new);
+  disp[t] = dn;
+  vel[t] = v_new;
+  acc[t] = a_new;
+  hist[t] = dn / (beta * dt * dt) + v_new / (beta * dt) + (1.0 - 2.0 * beta) / (2.0 * beta) * a_new;
+}
+
 }  // namespace
+
+void launch_newmark(Handle& h, const double* state, double* disp, double* vel, double* acc, double* hist,
+                    double beta, double gamma, double dt, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_OTHER, s, newmark_kernel<<<blocks_for(3L * h.n_nodes, 256), 256, 0, s>>>(
+      h.n_nodes, state, disp, vel, acc, hist, beta, gamma, dt));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
 
 void launch_geometry(Handle& h, cudaStream_t s) {
   if (h.n_elems == 0) return;
@@ -489,6 +606,56 @@ void launch_external_force(Handle& h, const fsi_load* load, cudaStream_t s) {
 
 void launch_assemble(Handle& h, const double* state, const double* hist, double* residual, bool want_tangent,
                      cudaStream_t s, void* vals_target, int target_fp32) {
+  if (h.opts.assembly == 0 && h.d_ebuf) {
+    launch_assemble_gather(h, state, hist, residual, want_tangent, s, vals_target, target_fp32);
+    return;
+  }
+  launch_assemble_colour(h, state, hist, residual, want_tangent, s, vals_target, target_fp32);
+}
+
+void launch_assemble_gather(Handle& h, const double* state, const double* hist, double* residual, bool want_tangent,
+                            cudaStream_t s, void* vals_target, int target_fp32) {
+  Level& L0 = h.levels[0];
+  void* vals = vals_target ? vals_target : L0.vals;
+  const bool f32 = vals_target ? (target_fp32 == 1) : (h.precision == FSI_PREC_FP32_IR);
+  const int ne = h.n_elems;
+  const int nbk = blocks_for(ne, kThreads);
+  double* er = residual ? h.d_rbuf : nullptr;
+  if (want_tangent && f32) {
+    FSI_LAUNCH(fsi::KC_TANGENT, s, element_buffer_kernel<float, float, true><<<nbk, kThreads, 0, s>>>(
+        ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
+        (float*)h.d_ebuf, (double*)nullptr, h.d_err));
+    if (er)
+      FSI_LAUNCH(fsi::KC_RESIDUAL, s, element_buffer_kernel<double, double, false><<<nbk, kThreads, 0, s>>>(
+          ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef,
+          h.opts.fibre_factor, (double*)nullptr, er, h.d_err));
+  } else if (want_tangent) {
+    FSI_LAUNCH(fsi::KC_TANGENT, s, element_buffer_kernel<double, double, true><<<nbk, kThreads, 0, s>>>(
+        ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
+        (double*)h.d_ebuf, er, h.d_err));
+  } else if (er) {
+    FSI_LAUNCH(fsi::KC_RESIDUAL, s, element_buffer_kernel<double, double, false><<<nbk, kThreads, 0, s>>>(
+        ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
+        (double*)nullptr, er, h.d_err));
+  }
+  if (want_tangent) {
+    if (f32)
+      FSI_LAUNCH(fsi::KC_TANGENT, s, gather_tangent_kernel<float><<<blocks_for(16L * L0.nb, 256), 256, 0, s>>>(
+          L0.nb, h.d_gb_ptr, h.d_gb_src, (const float*)h.d_ebuf, L0.block_row, L0.col_idx, h.d_dir_mask,
+          (float*)vals));
+    else
+      FSI_LAUNCH(fsi::KC_TANGENT, s, gather_tangent_kernel<double><<<blocks_for(16L * L0.nb, 256), 256, 0, s>>>(
+          L0.nb, h.d_gb_ptr, h.d_gb_src, (const double*)h.d_ebuf, L0.block_row, L0.col_idx, h.d_dir_mask,
+          (double*)vals));
+  }
+  if (residual)
+    FSI_LAUNCH(fsi::KC_RESIDUAL, s, gather_residual_kernel<<<blocks_for(4L * h.n_nodes, 256), 256, 0, s>>>(
+        h.n_nodes, h.d_gn_ptr, h.d_gn_src, er, h.d_fext, h.d_dir_mask, residual));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_assemble_colour(Handle& h, const double* state, const double* hist, double* residual, bool want_tangent,
+                            cudaStream_t s, void* vals_target, int target_fp32) {
   Level& L0 = h.levels[0];
   void* vals = vals_target ? vals_target : L0.vals;
   const bool f32 = vals_target ? (target_fp32 == 1) : (h.precision == FSI_PREC_FP32_IR);

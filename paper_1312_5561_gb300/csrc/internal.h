@@ -103,6 +103,7 @@ struct Level {
   void* ptent = nullptr;         // T [n][bs*7] tentative prolongator rows
   uint8_t* freem = nullptr;      // [n*bs] 1 = free unknown
   double omega_p = 0.0;
+  void* dinv_f = nullptr;        // T [n][bs*bs] filtered block inverses (prolongator smoothing)
   int32_t* p_brow = nullptr;     // [p_nb] block row of each P block
   int32_t* w_ptr = nullptr;      // [p_nb+1]
   int32_t* w_k = nullptr;        // A blocks summed into each W = A P_t block
@@ -164,6 +165,13 @@ struct Handle {
   double* d_seg_b = nullptr;
   double* h_seg = nullptr;       // pinned [n_seg]
   int* d_err = nullptr;          // device error word (bit 0 inverted, bit 1 bounds)
+  // gather-based assembly: element buffers and fixed gather plans
+  void* d_ebuf = nullptr;        // T [n_elems][16][16] element tangent blocks
+  double* d_rbuf = nullptr;      // [n_elems][16] element residuals
+  int32_t* d_gb_ptr = nullptr;   // [n_b+1] contributions of each BSR block
+  int32_t* d_gb_src = nullptr;   // [16 n_elems] element block index 16 e + (4a + b)
+  int32_t* d_gn_ptr = nullptr;   // [n_nodes+1] contributions of each node
+  int32_t* d_gn_src = nullptr;   // [4 n_elems] element node index 4 e + a
 
   // AMG hierarchy (level 0 = assembled matrix)
   std::vector<Level> levels;
@@ -181,6 +189,7 @@ struct Handle {
   double* d_partial = nullptr;   // reduction partials [n_red_blocks * 72]
   double* d_dots = nullptr;      // [72]
   double* h_dots = nullptr;      // pinned host [72]
+  float2* d_xdf = nullptr;       // [ndof] double-float split of an FP64 vector (FP32 mode)
   float* d_xs = nullptr;         // FP32 vector scratch for the mixed precision preconditioner
   float* d_ys = nullptr;
   double* d_fext = nullptr;      // [n_nodes][3]
@@ -189,6 +198,10 @@ struct Handle {
   int red_blocks = 0;
 
   cudaStream_t stream = nullptr;
+  cudaGraphExec_t vc_exec = nullptr;   // captured V-cycle (use_graphs)
+  long long vc_kernels = 0;            // kernels in the captured V-cycle
+  long long amg_calls = 0;             // numeric set-ups requested (amg_lag bookkeeping)
+  bool filter_p = false;               // prolongator smoothing without u-p couplings (inertia)
   struct Profiler* prof_ptr() { return &prof; }
   Profiler prof;
 };
@@ -201,17 +214,25 @@ void launch_external_force(Handle& h, const fsi_load* load, cudaStream_t s);
 // the tangent goes to level 0 (or to vals_target, FP32 if target_fp32 == 1).
 void launch_assemble(Handle& h, const double* state, const double* hist, double* residual,
                      bool want_tangent, cudaStream_t s, void* vals_target = nullptr, int target_fp32 = -1);
+void launch_assemble_gather(Handle& h, const double* state, const double* hist, double* residual,
+                            bool want_tangent, cudaStream_t s, void* vals_target, int target_fp32);
+void launch_assemble_colour(Handle& h, const double* state, const double* hist, double* residual,
+                            bool want_tangent, cudaStream_t s, void* vals_target, int target_fp32);
 void launch_set_dirichlet_values(Handle& h, double* state, const double* values, cudaStream_t s);
+void launch_newmark(Handle& h, const double* state, double* disp, double* vel, double* acc, double* hist,
+                    double beta, double gamma, double dt, cudaStream_t s);
 
 // linalg.cu
 template <typename T>
 void launch_spmv(const Level& L, const T* x, T* y, cudaStream_t s);
 void launch_spmv_f64acc(const Level& L, const double* x, double* y, bool fp32vals, cudaStream_t s);
+// FP32 values with FP64 vectors in double-float arithmetic; y = A x (b == nullptr) or y = b - A x
+void launch_spmv_df(const Level& L, const double* x, float2* xs, const double* b, double* y, cudaStream_t s);
 void launch_residual_f64(const Level& L, const double* b, const double* x, double* r, bool fp32vals,
                          cudaStream_t s);
 void launch_block_inverse(Level& L, bool fp32, int* err, cudaStream_t s);
 // numeric set-up of level+1 from level (smoothed P, P^T, A P, P^T A P)
-void launch_galerkin(Level& L, Level& C, bool fp32, cudaStream_t s);
+void launch_galerkin(Level& L, Level& C, bool fp32, bool filter, cudaStream_t s);
 void launch_coarse_factor(Handle& h, bool fp32, cudaStream_t s);
 template <typename T>
 void vcycle(Handle& h, int level, cudaStream_t s);

@@ -155,6 +155,68 @@ __global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const in
   }
 }
 
+// ---- FP64-accurate operator with FP32 values, without the FP64 pipe.
+// x (FP64) is first split into a pair of floats xh + xl (|xl| <= ulp(xh)/2).
+// Each product a * xh is formed exactly as p + e (p = a*xh, e = fma(a, xh, -p)),
+// a * xl is added as a plain FP32 product, and the row sum is carried as an
+// unevaluated pair of floats (Knuth's two-sum; Dekker/Knuth double-float
+// arithmetic), giving ~46-bit accuracy for ~10 FP32 operations per product.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF s, float p) {
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);   // two-sum error of s.hi + p
+  const float lo = s.lo + err;
+  const float hi = t + lo;
+  return DF{hi, lo - (hi - t)};
+}
+
+__global__ void split_df_kernel(const double* __restrict__ x, float2* __restrict__ xs, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double v = x[t];
+    const float h = (float)v;
+    xs[t] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+// MODE 0: y = A x, MODE 1: y = b - A x; A: FP32 4x4 blocks, x given as float pairs.
+template <int MODE>
+__global__ void bsr_df_kernel(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                              const float* __restrict__ vals, const float2* __restrict__ xs,
+                              const double* __restrict__ b, double* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t >> 2, r = t & 3;
+  if (row >= n) return;
+  DF s{0.f, 0.f};
+  float small = 0.f;
+  const int k1 = row_ptr[row + 1];
+  for (int k = row_ptr[row]; k < k1; ++k) {
+    const int j = col_idx[k];
+    const float4 a = *reinterpret_cast<const float4*>(vals + 16 * (size_t)k + 4 * r);
+    const float4 x01 = *reinterpret_cast<const float4*>(xs + 4 * (size_t)j);
+    const float4 x23 = *reinterpret_cast<const float4*>(xs + 4 * (size_t)j + 2);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float xh[4] = {x01.x, x01.z, x23.x, x23.z};
+    const float xl[4] = {x01.y, x01.w, x23.y, x23.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float p = av[c] * xh[c];
+      const float e = fmaf(av[c], xh[c], -p);
+      s = df_add(s, p);
+      small = fmaf(av[c], xl[c], small + e);
+    }
+  }
+  const double acc = (double)s.hi + ((double)s.lo + (double)small);
+  const size_t o = 4 * (size_t)row + r;
+  if (MODE == 0)
+    y[o] = acc;
+  else
+    y[o] = b[o] - acc;
+}
+
 // x = omega D^-1 b (first Jacobi sweep from a zero guess), B x B blocks
 template <typename T, int B>
 __global__ void jacobi_zero_kernel(int n, const T* __restrict__ dinv, const T* __restrict__ b, T omega,
@@ -170,8 +232,15 @@ __global__ void jacobi_zero_kernel(int n, const T* __restrict__ dinv, const T* _
   x[(size_t)row * B + r] = omega * acc;
 }
 
-// Inverse of each B x B diagonal block (Gauss-Jordan, partial pivoting, FP64).
-template <typename T, int B>
+// number of displacement-like unknowns in a B-block (3 of 4, 6 of 7)
+template <int B>
+struct NU {
+  static constexpr int v = (B == 4) ? 3 : 6;
+};
+
+// Inverse of each B x B diagonal block (Gauss-Jordan, partial pivoting, FP64);
+// FILTER drops the displacement-pressure couplings first.
+template <typename T, int B, bool FILTER = false>
 __global__ void block_inverse_kernel(int n, const int32_t* __restrict__ diag_idx, const T* __restrict__ vals,
                                      T* __restrict__ dinv, int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,7 +249,7 @@ __global__ void block_inverse_kernel(int n, const int32_t* __restrict__ diag_idx
   const T* v = vals + (size_t)(B * B) * diag_idx[i];
   for (int r = 0; r < B; ++r)
     for (int c = 0; c < B; ++c) {
-      a[r][c] = (double)v[B * r + c];
+      a[r][c] = (FILTER && ((r < NU<B>::v) != (c < NU<B>::v))) ? 0.0 : (double)v[B * r + c];
       a[r][B + c] = (r == c) ? 1.0 : 0.0;
     }
   bool ok = true;
@@ -203,13 +272,14 @@ __global__ void block_inverse_kernel(int n, const int32_t* __restrict__ diag_idx
   T* o = dinv + (size_t)(B * B) * i;
   for (int r = 0; r < B; ++r)
     for (int c = 0; c < B; ++c) o[B * r + c] = ok ? (T)a[r][B + c] : T(0);
-  if (!ok) atomicOr(err, 4);
+  if (!ok && err) atomicOr(err, 4);
 }
 
 constexpr int NS = 7;
 
-// W[q] = sum over the plan of A_k P_t(col(k))   (B x B times B x 7)
-template <typename T, int B>
+// W[q] = sum over the plan of A_k P_t(col(k))   (B x B times B x 7); FILTER
+// skips the displacement-pressure couplings of A.
+template <typename T, int B, bool FILTER>
 __global__ void galerkin_w_kernel(int p_nb, const int32_t* __restrict__ w_ptr, const int32_t* __restrict__ w_k,
                                   const int32_t* __restrict__ a_ci, const T* __restrict__ a_v,
                                   const T* __restrict__ ptent, T* __restrict__ w_v) {
@@ -223,7 +293,8 @@ __global__ void galerkin_w_kernel(int p_nb, const int32_t* __restrict__ w_ptr, c
     const T* a = a_v + (size_t)k * (B * B) + r * B;
     const T* p = ptent + (size_t)a_ci[k] * (B * NS) + c;
 #pragma unroll
-    for (int m = 0; m < B; ++m) acc += a[m] * p[m * NS];
+    for (int m = 0; m < B; ++m)
+      if (!FILTER || ((r < NU<B>::v) == (m < NU<B>::v))) acc += a[m] * p[m * NS];
   }
   w_v[(size_t)q * (B * NS) + e] = acc;
 }
@@ -557,6 +628,22 @@ void launch_spmv(const Level& L, const T* x, T* y, cudaStream_t s) {
 template void launch_spmv<double>(const Level&, const double*, double*, cudaStream_t);
 template void launch_spmv<float>(const Level&, const float*, float*, cudaStream_t);
 
+void split_df(const double* x, float2* xs, long n, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, split_df_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, xs, n));
+}
+
+// FP32 values, FP64 vectors: double-float accumulation (xs is scratch of 4 n float2)
+void launch_spmv_df(const Level& L, const double* x, float2* xs, const double* b, double* y, cudaStream_t s) {
+  split_df(x, xs, 4L * L.n, s);
+  if (b)
+    FSI_LAUNCH(fsi::KC_BSR0, s, bsr_df_kernel<1><<<blocks_for(4L * L.n, 128), 128, 0, s>>>(
+        L.n, L.row_ptr, L.col_idx, (const float*)L.vals, xs, b, y));
+  else
+    FSI_LAUNCH(fsi::KC_BSR0, s, bsr_df_kernel<0><<<blocks_for(4L * L.n, 128), 128, 0, s>>>(
+        L.n, L.row_ptr, L.col_idx, (const float*)L.vals, xs, nullptr, y));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
 void launch_spmv_f64acc(const Level& L, const double* x, double* y, bool fp32vals, cudaStream_t s) {
   if (fp32vals)
     bsr_launch<float, double, double, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, 0.0, y, s, fsi::KC_BSR0);
@@ -593,12 +680,21 @@ void launch_block_inverse(Level& L, bool fp32, int* err, cudaStream_t s) {
 }
 
 template <typename T, int B>
-static void galerkin_t(Level& L, Level& C, cudaStream_t s) {
+static void galerkin_t(Level& L, Level& C, bool filter, cudaStream_t s) {
   const long pe = (long)L.p_nb * B * NS;
-  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_w_kernel<T, B><<<blocks_for(pe, 256), 256, 0, s>>>(L.p_nb, L.w_ptr, L.w_k, L.col_idx, (const T*)L.vals,
-                                                              (const T*)L.ptent, (T*)L.w_v));
+  const T* dsm = (const T*)L.dinv;
+  if (filter) {
+    FSI_LAUNCH(fsi::KC_GALERKIN, s, block_inverse_kernel<T, B, true><<<blocks_for(L.n, 64), 64, 0, s>>>(
+        L.n, L.diag_idx, (const T*)L.vals, (T*)L.dinv_f, nullptr));
+    dsm = (const T*)L.dinv_f;
+    FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_w_kernel<T, B, true><<<blocks_for(pe, 256), 256, 0, s>>>(
+        L.p_nb, L.w_ptr, L.w_k, L.col_idx, (const T*)L.vals, (const T*)L.ptent, (T*)L.w_v));
+  } else {
+    FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_w_kernel<T, B, false><<<blocks_for(pe, 256), 256, 0, s>>>(
+        L.p_nb, L.w_ptr, L.w_k, L.col_idx, (const T*)L.vals, (const T*)L.ptent, (T*)L.w_v));
+  }
   FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_p_kernel<T, B><<<blocks_for(pe, 256), 256, 0, s>>>(L.p_nb, L.p_brow, L.p_ci, L.agg, L.freem,
-                                                              (const T*)L.dinv, (const T*)L.ptent, (const T*)L.w_v,
+                                                              dsm, (const T*)L.ptent, (const T*)L.w_v,
                                                               (T)L.omega_p, (T*)L.p_v));
   FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_pt_kernel<T, B><<<blocks_for(pe, 256), 256, 0, s>>>(L.p_nb, L.pt_src, (const T*)L.p_v, (T*)L.pt_v));
   FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_kernel<T, B><<<blocks_for((long)L.ap_nb * B * NS, 256), 256, 0, s>>>(
@@ -609,11 +705,11 @@ static void galerkin_t(Level& L, Level& C, cudaStream_t s) {
     FSI_LAUNCH(fsi::KC_GALERKIN, s, identity_fix_kernel<T><<<blocks_for(L.n_fix, 128), 128, 0, s>>>(L.n_fix, L.fix_blk, L.fix_dof, (T*)C.vals));
 }
 
-void launch_galerkin(Level& L, Level& C, bool fp32, cudaStream_t s) {
+void launch_galerkin(Level& L, Level& C, bool fp32, bool filter, cudaStream_t s) {
   if (fp32) {
-    if (L.bs == 4) galerkin_t<float, 4>(L, C, s); else galerkin_t<float, 7>(L, C, s);
+    if (L.bs == 4) galerkin_t<float, 4>(L, C, filter, s); else galerkin_t<float, 7>(L, C, filter, s);
   } else {
-    if (L.bs == 4) galerkin_t<double, 4>(L, C, s); else galerkin_t<double, 7>(L, C, s);
+    if (L.bs == 4) galerkin_t<double, 4>(L, C, filter, s); else galerkin_t<double, 7>(L, C, filter, s);
   }
   FSI_CUDA_TRY(cudaGetLastError());
 }

@@ -174,8 +174,9 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
 
   std::vector<HostLevel> hl;
   HostCoarse hc;
+  h.filter_p = h.opts.inertia_coef > 0.0;
   build_sa_hierarchy(A0, free0, X, comp0, std::max(1, h.opts.coarse_max_nodes), std::max(1, h.opts.max_levels),
-                     8, hl, hc);
+                     8, h.filter_p, hl, hc);
   const int nl = (int)hl.size();
   const size_t ts = f32 ? 4 : 8;
   for (int l = 1; l < nl; ++l) {
@@ -214,6 +215,7 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
     L.w_ptr = upload(H.w_ptr, s);
     L.w_k = upload(H.w_k, s);
     L.w_v = dalloc<char>(ts * (size_t)L.p_nb * bs * 7);
+    if (h.filter_p) L.dinv_f = dalloc<char>(ts * (size_t)L.n * bs * bs);
     L.ap_nb = H.AP.nb();
     L.ap_ptr = upload(H.ap_ptr, s);
     L.ap_pairs = upload(H.ap_pairs, s);
@@ -239,14 +241,53 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
 // Per Newton step, from the current tangent: block-Jacobi inverses, smoothed
 // prolongators and Galerkin operators of every level, and the dense inverse
 // of the coarsest operator.
+// With amg_lag = L > 0 the coarse levels (smoothed P, Galerkin operators,
+// coarsest factorisation) are recomputed only on every (L+1)-th call; the
+// finest level always uses the current K and its current block inverses.
 void amg_numeric(Handle& h, cudaStream_t s) {
   const bool f32 = h.precision == FSI_PREC_FP32_IR;
   const int nl = (int)h.levels.size();
+  launch_block_inverse(h.levels[0], f32, h.d_err, s);
+  const bool refresh = h.opts.amg_lag <= 0 || (h.amg_calls % (h.opts.amg_lag + 1)) == 0;
+  ++h.amg_calls;
+  if (!refresh) return;
   for (int l = 0; l + 1 < nl; ++l) {
-    launch_block_inverse(h.levels[l], f32, h.d_err, s);
-    launch_galerkin(h.levels[l], h.levels[l + 1], f32, s);
+    if (l > 0) launch_block_inverse(h.levels[l], f32, h.d_err, s);
+    launch_galerkin(h.levels[l], h.levels[l + 1], f32, h.filter_p, s);
   }
   launch_coarse_factor(h, f32, s);
+}
+
+// The V-cycle reads and writes only level buffers whose addresses are fixed
+// for the life of the handle, so it can be captured once into a CUDA graph and
+// replayed on any stream (use_graphs).  Kernel event timing is suspended while
+// capturing, so a replayed V-cycle is not split by kernel class.
+void run_vcycle(Handle& h, cudaStream_t s) {
+  const bool f32 = h.precision == FSI_PREC_FP32_IR;
+  // while kernel timing is recording, launch eagerly so that every kernel is timed
+  if (!h.opts.use_graphs || (g_prof && g_prof->on)) {
+    if (f32) vcycle<float>(h, 0, s); else vcycle<double>(h, 0, s);
+    return;
+  }
+  if (!h.vc_exec) {
+    Profiler* saved = g_prof;
+    g_prof = nullptr;
+    const long long l0 = g_launches;
+    cudaGraph_t graph = nullptr;
+    FSI_CUDA_TRY(cudaStreamSynchronize(h.stream));
+    FSI_CUDA_TRY(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
+    if (f32) vcycle<float>(h, 0, h.stream); else vcycle<double>(h, 0, h.stream);
+    cudaError_t e = cudaStreamEndCapture(h.stream, &graph);
+    g_prof = saved;
+    FSI_CUDA_TRY(e);
+    h.vc_kernels = g_launches - l0;
+    g_launches = l0;
+    e = cudaGraphInstantiate(&h.vc_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    FSI_CUDA_TRY(e);
+  }
+  FSI_CUDA_TRY(cudaGraphLaunch(h.vc_exec, s));
+  g_launches += h.vc_kernels;
 }
 
 // z = M^-1 v (one V-cycle)
@@ -255,29 +296,43 @@ void precondition(Handle& h, const double* v, double* z, cudaStream_t s) {
   const long n = 4L * L0.n;
   if (h.precision == FSI_PREC_FP32_IR) {
     to_float(v, (float*)L0.b, n, s);
-    vcycle<float>(h, 0, s);
+    run_vcycle(h, s);
     to_double((const float*)L0.x, z, n, s);
   } else {
     FSI_CUDA_TRY(cudaMemcpyAsync(L0.b, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    vcycle<double>(h, 0, s);
+    run_vcycle(h, s);
     FSI_CUDA_TRY(cudaMemcpyAsync(z, L0.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   }
 }
 
+// y = K x (FP64 vectors).  With FP32 values the sum is carried in
+// double-float arithmetic; with FP64 values in FP64.
 void apply_operator(Handle& h, const double* x, double* y, cudaStream_t s) {
-  launch_spmv_f64acc(h.levels[0], x, y, h.precision == FSI_PREC_FP32_IR, s);
+  if (h.precision == FSI_PREC_FP32_IR)
+    launch_spmv_df(h.levels[0], x, h.d_xdf, nullptr, y, s);
+  else
+    launch_spmv_f64acc(h.levels[0], x, y, false, s);
+}
+
+void operator_residual(Handle& h, const double* b, const double* x, double* r, cudaStream_t s) {
+  if (h.precision == FSI_PREC_FP32_IR)
+    launch_spmv_df(h.levels[0], x, h.d_xdf, b, r, s);
+  else
+    launch_residual_f64(h.levels[0], b, x, r, false, s);
 }
 
 // FGMRES(m), right preconditioned.  Returns iterations; *rel = ||b - A x|| / ||b||.
+// Orthogonalisation: classical Gram-Schmidt applied twice (one pass alone lost
+// enough orthogonality here to multiply the iteration count by 2.5).  The new
+// direction is formed in place in V_(j+1), so each reduction also returns
+// ||w||^2 and the norm after the second pass follows from Pythagoras.
 int fgmres(Handle& h, const double* b, double* x, double rtol, int maxit, double* rel, cudaStream_t s) {
   const long n = 4L * h.n_nodes;
   const int m = h.m;
-  const bool f32 = h.precision == FSI_PREC_FP32_IR;
   double* V = h.d_V;
   double* Z = h.d_Z;
-  double* w = h.d_w;
   double* r = h.d_r;
-  launch_residual_f64(h.levels[0], b, x, r, f32, s);
+  operator_residual(h, b, x, r, s);
   const double bnorm = norm2_host(h, b, n, s);
   double beta = norm2_host(h, r, n, s);
   if (bnorm == 0.0) {
@@ -296,20 +351,38 @@ int fgmres(Handle& h, const double* b, double* x, double rtol, int maxit, double
     for (int j = 0; j < m; ++j) {
       double* vj = V + (size_t)j * n;
       double* zj = Z + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
       precondition(h, vj, zj, s);
       apply_operator(h, zj, w, s);
-      // classical Gram-Schmidt, twice
-      dots(h, V, n, j + 1, w, n, h.d_dots, s);
-      multi_axpy(h.d_dots, V, j + 1, n, w, -1.0, s);
-      dots(h, V, n, j + 1, w, n, h.d_dots + kDotH2, s);
-      multi_axpy(h.d_dots + kDotH2, V, j + 1, n, w, -1.0, s);
-      dots(h, w, 0, 1, w, n, h.d_dots + kDotW, s);
-      FSI_CUDA_TRY(cudaMemcpyAsync(h.h_dots, h.d_dots, sizeof(double) * (kDotW + 1), cudaMemcpyDeviceToHost, s));
+      // pass 1: h = V^T w and ||w||^2 in one reduction (w is vector j+1)
+      dots(h, V, n, j + 2, w, n, h.d_dots, s);
+      FSI_CUDA_TRY(cudaMemcpyAsync(h.h_dots, h.d_dots, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
       FSI_CUDA_TRY(cudaStreamSynchronize(s));
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h.h_dots[i] + h.h_dots[kDotH2 + i];
-      const double hn = std::sqrt(std::max(h.h_dots[kDotW], 0.0));
+      const double w2 = h.h_dots[j + 1];
+      double proj = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        H[(size_t)i * m + j] = h.h_dots[i];
+        proj += h.h_dots[i] * h.h_dots[i];
+      }
+      multi_axpy(h.d_dots, V, j + 1, n, w, -1.0, s);
+      double hn2 = w2 - proj;
+      {
+        // pass 2
+        dots(h, V, n, j + 2, w, n, h.d_dots + kDotH2, s);
+        FSI_CUDA_TRY(cudaMemcpyAsync(h.h_dots + kDotH2, h.d_dots + kDotH2, sizeof(double) * (j + 2),
+                                     cudaMemcpyDeviceToHost, s));
+        FSI_CUDA_TRY(cudaStreamSynchronize(s));
+        double proj2 = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          H[(size_t)i * m + j] += h.h_dots[kDotH2 + i];
+          proj2 += h.h_dots[kDotH2 + i] * h.h_dots[kDotH2 + i];
+        }
+        multi_axpy(h.d_dots + kDotH2, V, j + 1, n, w, -1.0, s);
+        hn2 = h.h_dots[kDotH2 + j + 1] - proj2;
+      }
+      const double hn = std::sqrt(std::max(hn2, 0.0));
       H[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0) scale_copy(1.0 / hn, w, V + (size_t)(j + 1) * n, n, s);
+      if (hn > 0.0) scale_copy(1.0 / hn, w, w, n, s);
       // Givens rotations
       for (int i = 0; i < j; ++i) {
         double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
@@ -337,7 +410,7 @@ int fgmres(Handle& h, const double* b, double* x, double rtol, int maxit, double
     }
     FSI_CUDA_TRY(cudaMemcpyAsync(h.d_dots + kDotY, y.data(), sizeof(double) * jj, cudaMemcpyHostToDevice, s));
     multi_axpy(h.d_dots + kDotY, Z, jj, n, x, 1.0, s);
-    launch_residual_f64(h.levels[0], b, x, r, f32, s);
+    operator_residual(h, b, x, r, s);
     beta = norm2_host(h, r, n, s);
   }
   *rel = beta / bnorm;
@@ -479,6 +552,27 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
   launch_geometry(h, s);
   if (check_err(h, s) & 1) throw ArgError("an element has non-positive reference volume");
 
+  // gather plans (deterministic assembly without colours): contributions of
+  // each block / node in element order
+  {
+    std::vector<int32_t> bptr(L0.hpat.col_idx.size() + 1, 0), bsrc(16 * (size_t)ne);
+    for (size_t q = 0; q < slot.size(); ++q) bptr[slot[q] + 1]++;
+    for (size_t b = 0; b + 1 < bptr.size(); ++b) bptr[b + 1] += bptr[b];
+    std::vector<int32_t> fill(bptr.begin(), bptr.end() - 1);
+    for (size_t q = 0; q < slot.size(); ++q) bsrc[fill[slot[q]]++] = (int32_t)q;
+    std::vector<int32_t> nptr(nn + 1, 0), nsrc(4 * (size_t)ne);
+    for (size_t q = 0; q < conn.size(); ++q) nptr[conn[q] + 1]++;
+    for (int i = 0; i < nn; ++i) nptr[i + 1] += nptr[i];
+    std::vector<int32_t> fn(nptr.begin(), nptr.end() - 1);
+    for (size_t q = 0; q < conn.size(); ++q) nsrc[fn[conn[q]]++] = (int32_t)q;
+    h.d_gb_ptr = upload(bptr, s);
+    h.d_gb_src = upload(bsrc, s);
+    h.d_gn_ptr = upload(nptr, s);
+    h.d_gn_src = upload(nsrc, s);
+    h.d_ebuf = dalloc<char>((size_t)ne * 256 * 8);   // FP64 size: the reference tangent is FP64
+    h.d_rbuf = dalloc<double>((size_t)ne * 16);
+    FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   upload_pattern(L0, s);
   L0.bs = 4;
   L0.cmask = h.d_dir_mask;
@@ -496,6 +590,7 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
   h.d_t2 = dalloc<double>(ndof);
   h.d_t3 = dalloc<double>(ndof);
   h.d_res = dalloc<double>(ndof);
+  h.d_xdf = dalloc<float2>(ndof);
   h.d_state_tmp = dalloc<double>(ndof);
   h.d_fext = dalloc<double>(3 * (size_t)nn);
   FSI_CUDA_TRY(cudaMemsetAsync(h.d_fext, 0, sizeof(double) * 3 * nn, s));
@@ -516,18 +611,20 @@ static void destroy_impl(Handle* hp) {
     for (void* p : {(void*)L.row_ptr, (void*)L.col_idx, (void*)L.diag_idx, (void*)L.block_row, L.vals, L.dinv,
                     (void*)L.p_rp, (void*)L.p_ci, L.p_v, (void*)L.pt_rp, (void*)L.pt_ci, L.pt_v, L.x, L.x2, L.b,
                     L.r, (void*)L.agg, L.ptent, (void*)L.freem, (void*)L.p_brow, (void*)L.w_ptr, (void*)L.w_k,
-                    L.w_v, (void*)L.pt_src, (void*)L.ap_ptr, (void*)L.ap_pairs, L.ap_v, (void*)L.ac_ptr,
+                    L.w_v, L.dinv_f, (void*)L.pt_src, (void*)L.ap_ptr, (void*)L.ap_pairs, L.ap_v, (void*)L.ac_ptr,
                     (void*)L.ac_pairs, (void*)L.fix_blk, (void*)L.fix_dof})
       dfree(p);
   }
   for (void* p : {(void*)h.coarse.comp_ptr, (void*)h.coarse.inv_off, h.coarse.inv, (void*)h.coarse.work,
                   (void*)h.d_conn, (void*)h.d_geo, (void*)h.d_fibre, (void*)h.d_mat, (void*)h.d_slot,
                   (void*)h.d_mats, (void*)h.d_X, (void*)h.d_dir_mask, (void*)h.d_faces, (void*)h.d_nf_ptr,
-                  (void*)h.d_nf_idx, (void*)h.d_seg_node, (void*)h.d_err, (void*)h.d_V, (void*)h.d_Z,
+                  (void*)h.d_nf_idx, (void*)h.d_seg_node, h.d_ebuf, (void*)h.d_rbuf, (void*)h.d_gb_ptr,
+                  (void*)h.d_gb_src, (void*)h.d_gn_ptr, (void*)h.d_gn_src, (void*)h.d_err, (void*)h.d_V, (void*)h.d_Z,
                   (void*)h.d_w, (void*)h.d_r, (void*)h.d_t, (void*)h.d_t2, (void*)h.d_t3, (void*)h.d_partial,
-                  (void*)h.d_dots, (void*)h.d_xs, (void*)h.d_ys, (void*)h.d_fext, (void*)h.d_state_tmp,
+                  (void*)h.d_dots, (void*)h.d_xdf, (void*)h.d_xs, (void*)h.d_ys, (void*)h.d_fext, (void*)h.d_state_tmp,
                   (void*)h.d_res})
     dfree(p);
+  if (h.vc_exec) cudaGraphExecDestroy(h.vc_exec);
   if (h.h_dots) cudaFreeHost(h.h_dots);
   if (h.h_seg) cudaFreeHost(h.h_seg);
   dfree(h.d_seg_ptr);
@@ -713,7 +810,8 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->max_levels = 12;
   o->use_pspg = 1;
   o->adaptive_tol = 0;
-  o->use_graphs = 0;
+  o->use_graphs = 1;
+  o->amg_lag = 0;
   o->omega = 0.7;
   o->newton_rtol = 1e-8;
   o->krylov_rtol = 1e-8;
@@ -854,6 +952,19 @@ fsi_status fsi_solid_solve(fsi_solid_t hh, double* state, const fsi_load* load, 
   if (info) info->status = st;
   if (st) fsi::set_error(h, st == FSI_ERR_INVERTED ? "inverted or non-finite element" : "Newton did not converge");
   return (fsi_status)st;
+  FSI_GUARD_END(h)
+}
+
+fsi_status fsi_solid_newmark_advance(fsi_solid_t hh, const double* state, double* disp, double* vel, double* acc,
+                                     double* hist, double beta, double gamma, double dt, void* stream) {
+  Handle* h = H(hh);
+  if (!h || !state || !disp || !vel || !acc || !hist || !(beta > 0) || !(dt > 0)) return FSI_ERR_ARG;
+  FSI_GUARD_BEGIN
+  FSI_PROF(h);
+  cudaStream_t s = S(h, stream);
+  fsi::launch_newmark(*h, state, disp, vel, acc, hist, beta, gamma, dt, s);
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  return FSI_OK;
   FSI_GUARD_END(h)
 }
 

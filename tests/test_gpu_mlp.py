@@ -1,0 +1,89 @@
+"""The learned-guess MLP kernels (forward, backward, Adam, BF16 inference)
+against the FP64 oracle, and the learned guess against plain Newton."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params]).astype(np.float32)
+
+
+def _unflat(flat, sizes):
+    out, off = [], 0
+    for fin, fout in zip(sizes[:-1], sizes[1:]):
+        W = flat[off:off + fin * fout].reshape(fout, fin).astype(np.float64)
+        off += fin * fout
+        b = flat[off:off + fout].astype(np.float64)
+        off += fout
+        out.append([W, b])
+    return out
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_1312_5561_gb300.binding import Mlp
+    sizes = [16, 48, 32, 32, 4]
+    net = Mlp(sizes, seed=3)
+    rng = np.random.default_rng(0)
+    params = _unflat(net.get_params(), sizes)
+    for W, b in params:
+        b[:] = 0.1 * rng.standard_normal(b.shape)
+    net.set_params(_flat(params))
+    params = _unflat(_flat(params), sizes)            # FP32-rounded, as on the device
+    X = rng.standard_normal((1000, 16)).astype(np.float32)
+    T = rng.standard_normal((1000, 4)).astype(np.float32)
+    return net, sizes, params, X, T
+
+
+def test_forward_fp32_and_bf16(case):
+    net, sizes, params, X, T = case
+    Xd = torch.tensor(X, device="cuda")
+    ref, _, _ = M.forward(params, X.astype(np.float64))
+    y32 = net.forward(Xd).cpu().numpy()
+    assert np.abs(y32 - ref).max() <= 1e-5 * np.abs(ref).max()
+    y16 = net.forward(Xd, bf16=True).cpu().numpy()
+    assert np.abs(y16 - ref).max() <= 3e-2 * np.abs(ref).max()
+
+
+def test_gradients_match_the_oracle(case):
+    net, sizes, params, X, T = case
+    loss, g = net.train_step(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"), apply=False,
+                             want_grad=True)
+    loss_ref, grads = M.loss_and_grads(params, X.astype(np.float64), T.astype(np.float64))
+    gref = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+    assert np.abs(g - gref).max() <= 1e-4 * np.abs(gref).max()
+
+
+def test_adam_step_matches_the_oracle(case):
+    net, sizes, params, X, T = case
+    before = net.get_params()
+    p = _unflat(before, sizes)
+    _, grads = M.loss_and_grads(p, X.astype(np.float64), T.astype(np.float64))
+    net.train_step(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"), lr=1e-3)
+    after = net.get_params()
+    M.adam_step(p, grads, {}, lr=1e-3)
+    gref = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+    clear = np.abs(gref) > 1e-3 * np.abs(gref).max()   # FP32 cannot fix the sign of tiny gradients
+    assert np.abs(after - _flat(p))[clear].max() <= 1e-6
+    assert np.abs(after - before).max() <= 1e-3 * (1 + 1e-5)
+    net.set_params(before)
+
+
+def test_learned_guess_saves_newton_iterations():
+    """Small artery (64x8x8 hexes), Newmark dt = 0.01, p(t) with noise: train on
+    the first 140 steps, replay the next 40 with each initial guess."""
+    from fixtures import artery_layers, artery_tube
+    from paper_1312_5561_gb300.learned_guess import run_study
+    mesh = artery_tube(n_theta=64, n_z=8, length=0.5, materials=artery_layers(1.0e3, rho=1.2))
+    out = run_study(mesh, n_steps=180, n_train=140, train_steps=1500, nodes_per_step=2048)
+    r = out["results"]
+    print(out)
+    assert out["loss_last"] < 0.5 * out["loss_first"]
+    assert r["mlp"]["mean_newton_its"] < r["zero"]["mean_newton_its"]
+    assert r["mlp"]["mean_newton_its"] <= r["linear_extrapolation"]["mean_newton_its"] + 0.1
