@@ -53,6 +53,9 @@ def workload_mesh(nz=128, config="tube", nseg=256):
     from fixtures import artery_layers, artery_tube, batched_tubes
     if config == "batched":
         return batched_tubes(n_seg=nseg, seed=4)
+    if config == "refined":
+        return artery_tube(n_theta=128, n_media=8, n_adv=8, n_z=2 * nz, length=8.0 * nz / 128,
+                           materials=artery_layers(1.0e5))
     return artery_tube(n_theta=64, n_media=4, n_adv=4, n_z=nz, length=8.0 * nz / 128,
                        materials=artery_layers(1.0e3))
 
@@ -99,6 +102,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest value of x over all ranks (the step time every rank waits for)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps_per_s_max_time, world):
+    """Whole-job throughput of N independent replicas: N x the per-replica rate
+    measured with the slowest rank's time."""
+    return steps_per_s_max_time * world
+
+
 # ------------------------------------------------------------------ GPU arm
 def jacobi0_bytes(n, nb, fp32):
     """Algorithmic bytes of one finest-level damped block-Jacobi sweep:
@@ -121,6 +141,7 @@ class RampDriver:
         self.k = 1
         self.r0 = None
         self.newton_in_load = 0
+        self.krylov_cap_hits = 0       # Newton steps whose linear solve ended at max_krylov above tolerance
 
     def step(self, state=None):
         st = self.state if state is None else state
@@ -128,6 +149,7 @@ class RampDriver:
         info = self.solver.newton_step(st, self.Load(pressure=scale, face_pressure=self.fp), check=False)
         if info.status not in (0, -5):
             raise RuntimeError(f"newton_step failed with status {info.status}")
+        self.krylov_cap_hits += info.status == -5
         if self.r0 is None:
             self.r0 = info.res0
         self.newton_in_load += 1
@@ -148,8 +170,13 @@ def run_gpu(args, rank, world):
     mesh = workload_mesh(args.nz, args.config, args.nseg)
     prec = 1 if args.precision == "fp32" else 0
     t_create = time.perf_counter()
-    solver = SolidSolver(mesh, precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, max_krylov=600,
-                         use_graphs=int(args.graphs))
+    # fgmres-amg: FGMRES(100) + one AMG V-cycle on the whole u-p tangent;
+    # bicgstab-pl: the paper's solid solver, BiCGStab + block-triangular P_L (Sec. 4.4.2)
+    kry = dict(krylov=1, precond=1, max_krylov=3000) if args.solver == "bicgstab-pl" else dict(max_krylov=600)
+    if args.smoother == "vanka":       # the paper's Vanka smoother on the finest level (Sec. 4.5)
+        kry.update(smoother=1, vanka_omega=0.86, nu_pre=args.nu, nu_post=args.nu)
+    solver = SolidSolver(mesh, precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=int(args.graphs),
+                         amg_lag=int(args.amg_lag), **kry)
     t_create = time.perf_counter() - t_create
     levels = solver.levels()
     drv = RampDriver(solver, mesh.n_nodes, torch, getattr(mesh, "face_pressure", None))
@@ -164,6 +191,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     krylov = 0
+    caps0 = drv.krylov_cap_hits
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
@@ -173,6 +201,7 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = launch_count() - l0
+    cap_hits = drv.krylov_cap_hits - caps0
     ms_total = ev0.elapsed_time(ev1)
     # kernel-timing pass: the same Newton steps continued, with CUDA events recorded
     # on the launching stream around every launch (the V-cycle is then launched
@@ -182,10 +211,7 @@ def run_gpu(args, rank, world):
         drv.step()
     torch.cuda.synchronize()
     prof = solver.kernel_timing(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world)
     steps_per_s = args.steps / (ms_total * 1e-3)
 
     # element tangents / s (residual + tangent assembly, device resident)
@@ -236,7 +262,7 @@ def run_gpu(args, rank, world):
         "steps_per_s": steps_per_s, "ms_per_step": ms_total / args.steps, "tangents_per_s": tangents_per_s,
         "e2e_steps_per_s": e2e, "bytes": nbytes, "launches": launches, "clocks": clk,
         "prof": {k: [round(v[0], 3), v[1]] for k, v in prof.items()}, "dominant": dominant, "roofline": roof,
-        "krylov_per_step": krylov / args.steps, "levels": levels, "n_elems": mesh.n_elems,
+        "krylov_per_step": krylov / args.steps, "krylov_cap_hits": cap_hits, "levels": levels, "n_elems": mesh.n_elems,
         "n_nodes": mesh.n_nodes, "create_s": t_create,
     }
 
@@ -299,12 +325,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--nz", type=int, default=128)
-    ap.add_argument("--config", default="tube", choices=["tube", "batched"])
+    ap.add_argument("--config", default="tube", choices=["tube", "batched", "refined"])
+    ap.add_argument("--amg-lag", type=int, default=0, help="refresh the coarse AMG levels every (lag+1) steps")
     ap.add_argument("--nseg", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single", action="store_true", help="skip the plain-FP64 comparison run")
     ap.add_argument("--graphs", type=int, default=1, help="replay the V-cycle from a captured CUDA graph")
     ap.add_argument("--prof-steps", type=int, default=6, help="Newton steps of the kernel-timing pass")
+    ap.add_argument("--solver", default="fgmres-amg", choices=["fgmres-amg", "bicgstab-pl"])
+    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "vanka"])
+    ap.add_argument("--nu", type=int, default=1, help="Vanka sweeps before / after the coarse correction")
+    ap.add_argument("--compare-paper-solver", action="store_true",
+                    help="also time BiCGStab + P_L (the paper's solid solver) on the same workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -313,6 +345,10 @@ def main():
     full_elems = 64 * 8 * args.nz * 6
     wl = (f"two-layer artery tube 64x8x{args.nz} hex x6 tets ({full_elems} tets), kappa=1e3*c10, "
           f"pressure ramp 0->1.6 in 10 load steps")
+    if args.config == "refined":
+        full_elems = 128 * 16 * 2 * args.nz * 6
+        wl = (f"two-layer artery tube 128x16x{2 * args.nz} hex x6 tets ({full_elems} tets), kappa=1e5*c10, "
+              f"pressure ramp 0->1.6 in 10 load steps")
     if args.config == "batched":
         wl = (f"{args.nseg} independent artery segments in one handle (seed 4): n_e logU[5e3,2e5], angles U[20,70], "
               f"kappa/c10 logU[1e2,1e5], pressure U[0.5,2.0] ramped in 10 load steps")
@@ -323,7 +359,7 @@ def main():
         if rank != 0:
             return
         nz_s = 4
-        line = oracle_line(args, full_elems, nz_s, max(1, args.steps // 10), 1)
+        line = oracle_line(args, full_elems, nz_s, args.steps, args.warmup)
         ms = 1e3 / line["value"]
         out = {"impl": "reference", "metric": METRIC, "value": line["value"], "unit": "steps/s",
                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -344,16 +380,27 @@ def main():
         a2.precision = "fp64"
         a2.steps = max(5, args.steps // 2)
         other = run_gpu(a2, rank, world)
+    paper = None
+    if args.compare_paper_solver and args.solver != "bicgstab-pl":
+        a3 = argparse.Namespace(**vars(args))
+        a3.solver = "bicgstab-pl"
+        a3.steps = max(5, args.steps // 2)
+        paper = run_gpu(a3, rank, world)
     if rank != 0:
         return
-    value = res["steps_per_s"] * world
+    value = job_value(res["steps_per_s"], world)
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": dict(config, precision=("FP32 tangent + FP32 V-cycle under FP64 residual / outer FGMRES"
                                           if args.precision == "fp32" else "FP64 throughout"),
-                       krylov_its_per_step=round(res["krylov_per_step"], 1), amg_levels=res["levels"]),
+                       solver=("BiCGStab + block-triangular P_L (AMG V-cycle on A)" if args.solver == "bicgstab-pl"
+                               else "FGMRES(100) + AMG V-cycle on K"),
+                       finest_smoother=(f"Vanka, {args.nu}+{args.nu} sweeps, omega 0.86" if args.smoother == "vanka"
+                                        else "damped block Jacobi, 4+4 sweeps, omega 0.7"),
+                       krylov_its_per_step=round(res["krylov_per_step"], 1),
+                       krylov_cap_hits_in_timed_steps=res["krylov_cap_hits"], amg_levels=res["levels"]),
         "element_tangents_per_s": res["tangents_per_s"] * world,
         "e2e": {"value": res["e2e_steps_per_s"] * world, "unit": "steps/s",
                 "h2d_bytes_per_step": res["bytes"], "d2h_bytes_per_step": res["bytes"]},
@@ -370,6 +417,12 @@ def main():
                              "krylov_its_per_step": round(other["krylov_per_step"], 1),
                              "speedup_vs_plain_fp64": res["steps_per_s"] / other["steps_per_s"],
                              "roofline": other["roofline"], "dominant_kernel_class": other["dominant"]}
+    if paper is not None:
+        out["paper_solver"] = {"solver": "BiCGStab + block-triangular P_L (Sec. 4.4.2), same precision",
+                               "value": paper["steps_per_s"] * world, "ms_per_step": paper["ms_per_step"],
+                               "krylov_its_per_step": round(paper["krylov_per_step"], 1),
+                               "krylov_cap_hits_in_timed_steps": paper["krylov_cap_hits"],
+                               "speedup_of_ours": res["steps_per_s"] / paper["steps_per_s"]}
     if not args.no_cpu_baseline and world == 1:
         try:
             out["cpu_baseline"] = oracle_line(args, full_elems, 4, 2, 1)

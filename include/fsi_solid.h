@@ -81,7 +81,30 @@ typedef struct {
 
 enum { FSI_PREC_FP64 = 0, FSI_PREC_FP32_IR = 1 };
 enum { FSI_KRYLOV_FGMRES = 0, FSI_KRYLOV_BICGSTAB = 1 };
-enum { FSI_SMOOTHER_JACOBI = 0, FSI_SMOOTHER_CHEBYSHEV = 1 };
+/* Smoother of the finest AMG level (coarser levels always use damped block
+ * Jacobi).
+ *  FSI_SMOOTHER_JACOBI  damped 4x4 block Jacobi, damping omega.
+ *  FSI_SMOOTHER_VANKA   the multiplicative Vanka smoother of Sec. 4.5
+ *                       (Eq. locsys, vankasmooth): one patch per pressure
+ *                       unknown p_i holding p_i and the displacements of the
+ *                       nodes that B2 couples to it (node i and its mesh
+ *                       neighbours, up to 46 unknowns); the local problem is
+ *                       the restriction of K to the patch, solved directly, and
+ *                       the update is relaxed by vanka_omega.  Patches are
+ *                       visited colour by colour (distance-2 node colouring,
+ *                       so patches of one colour share no unknown): Gauss-Seidel
+ *                       across colours, simultaneous within a colour. */
+enum { FSI_SMOOTHER_JACOBI = 0, FSI_SMOOTHER_VANKA = 1 };
+/* Preconditioner of the Krylov method.
+ *  FSI_PRECOND_AMG       one AMG V-cycle on the whole u-p tangent K (default).
+ *  FSI_PRECOND_BLOCK_LT  the block lower-triangular P_L of Sec. 4.4.2,
+ *                        Eq. lpre: x_u = A~^-1 r_u by one AMG V-cycle on the
+ *                        displacement block A, then
+ *                        x_p = S~^-1 (B2 x_u - r_p) with the Schur-complement
+ *                        approximation S~ = (1/theta + 1/kappa) diag(M_p) of
+ *                        Eq. lpreschur (M_p the P1 pressure mass matrix, kappa
+ *                        per element).  The paper pairs it with BiCGStab. */
+enum { FSI_PRECOND_AMG = 0, FSI_PRECOND_BLOCK_LT = 1 };
 
 /* Solver options.  Defaults come from fsi_solid_default_opts(). */
 typedef struct {
@@ -93,7 +116,6 @@ typedef struct {
   int32_t max_newton;       /* cap on Newton iterations per solve */
   int32_t smoother;         /* FSI_SMOOTHER_* */
   int32_t nu_pre, nu_post;  /* smoothing sweeps before / after the coarse correction */
-  int32_t cheb_degree;      /* Chebyshev polynomial degree */
   int32_t coarse_max_nodes; /* stop coarsening when every component is this small */
   int32_t max_levels;       /* cap on AMG levels */
   int32_t use_pspg;         /* 1: PSPG term W_s of Eq. stelas on; 0: off */
@@ -110,6 +132,11 @@ typedef struct {
                                always the current tangent */
   int32_t assembly;         /* 0: element buffers + fixed-order gather (default);
                                1: colour-ordered scatter; both bit-reproducible */
+  int32_t precond;          /* FSI_PRECOND_* */
+  double schur_theta;       /* theta of Eq. lpreschur (the paper takes theta = O(c10));
+                               <= 0: c10 of material 0 */
+  double vanka_omega;       /* relaxation of the Vanka update (the paper: 0.78 for
+                               Mooney-Rivlin, 0.86 for the artery) */
 } fsi_solver_opts;
 
 /* Load of one solve (device arrays owned by the caller; NULL = absent).
@@ -193,6 +220,57 @@ fsi_status fsi_solid_newton_step(fsi_solid_t h, double* state, const fsi_load* l
  * else Newton starts from v (zero increment). */
 fsi_status fsi_solid_solve(fsi_solid_t h, double* state, const fsi_load* load, const double* guess,
                            fsi_info* info, void* stream);
+
+/* Partitioned coupling: the Dirichlet-Neumann iteration of Sec. 5.1 with the
+ * Aitken relaxation of Sec. 5.2 around fsi_solid_solve.  The interface Gamma^0
+ * is the set of vertices of the mesh's loaded faces (neu_faces).  Cycle k
+ * computes the fluid pressure from the relaxed interface displacement
+ * d_(k-1), solves the solid under it (Newton from the previous cycle's state,
+ * stopping relative to the first cycle's initial residual norm), takes
+ * d~_k = the solid displacement on Gamma^0 and r_k = d~_k - d_(k-1), stops when
+ * |r_k| / sqrt(n_Gamma) < tol, and relaxes d_k = w_(k-1) d~_k + (1 - w_(k-1)) d_(k-1)
+ * (Eq. acceit) with w_k = -w_(k-1) r_k.(r_(k+1) - r_k) / |r_(k+1) - r_k|^2
+ * (Eq. dnomega), w_0 = omega0.
+ *
+ * The fluid Dirichlet-to-Neumann map F of Eq. fixedp (a Navier-Stokes solve on
+ * the moving fluid domain) is not part of this library; a surrogate added-mass
+ * map of the blood column stands in for it: on interface node i
+ *   p_i = p0 - added_mass * w_i . (d_i - d_ref_i),
+ * w_i the unit direction of the P1 load of a unit pressure at node i.  The
+ * resulting nodal pressures load the loaded faces as fsi_load.node_pressure
+ * does.  With added_mass large against the wall stiffness, omega = 1 diverges
+ * (the added-mass effect); the Aitken step restores convergence. */
+typedef struct {
+  double p0;              /* fluid pressure at rest */
+  double added_mass;      /* >= 0, pressure per unit wall displacement */
+  const double* d_ref;    /* device [n_nodes][4] state whose displacement is the wall
+                             at rest (previous time level); NULL = reference configuration */
+  double omega0;          /* first relaxation factor, (0, 1] */
+  double tol;             /* interface residual tolerance (the paper: 1e-8) */
+  int32_t max_cycles;     /* cap on DN cycles */
+  int32_t aitken;         /* 1: Aitken (Eq. dnomega); 0: fixed omega0 */
+} fsi_dn_opts;
+
+typedef struct {
+  int32_t cycles;           /* DN cycles run */
+  int32_t converged;        /* 1 when |r| / sqrt(n_Gamma) < tol */
+  int32_t newton_its_total;
+  int32_t krylov_its_total;
+  int32_t n_interface;      /* n_Gamma */
+  double res_first;         /* |r_1| / sqrt(n_Gamma) */
+  double res_last;
+  double omega_last;        /* the last relaxation factor used */
+} fsi_dn_info;
+
+void fsi_dn_default_opts(fsi_dn_opts* o);
+
+/* state: device FP64 [n_nodes][4], start and result (the solid state of the
+ * last cycle).  load: dir_values and hist are used; its pressure fields are
+ * replaced by the fluid's.  Returns FSI_ERR_NOT_CONVERGED (info filled) when
+ * max_cycles end above tol, FSI_ERR_ARG without loaded faces or with
+ * omega0 outside (0, 1] or added_mass < 0, and any status of fsi_solid_solve. */
+fsi_status fsi_solid_dn_solve(fsi_solid_t h, double* state, const fsi_load* load, const fsi_dn_opts* o,
+                              fsi_dn_info* info, void* stream);
 
 /* Newmark-beta update after the solve of time step n (Sec. 4.1.2):
  *   a_n = (d_n - d_(n-1)) / (beta dt^2) - v_(n-1) / (beta dt) - (1 - 2 beta)/(2 beta) a_(n-1)

@@ -340,11 +340,12 @@ class Problem:
         s[m] = values[m]
         return s
 
-    def newton(self, state, fext=None, hist=None, rtol=1e-10, max_it=30, record=None):
+    def newton(self, state, fext=None, hist=None, rtol=1e-10, max_it=30, record=None, r_ref=None):
         """Newton's method (Sec. 4.4) with an exact sparse direct linear solve.
-        Stops when ||R(v_k)||_2 <= rtol ||R(v_0)||_2."""
+        Stops when ||R(v_k)||_2 <= rtol ||R(v_0)||_2, or rtol * r_ref when a
+        reference norm is given."""
         v = state.copy()
-        r0 = None
+        r0 = r_ref
         for k in range(max_it + 1):
             R = self.residual(v, fext, hist)
             rn = float(np.linalg.norm(R))

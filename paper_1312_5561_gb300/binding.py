@@ -29,7 +29,7 @@ EXPORTS = [
     "fsi_solid_solve", "fsi_solid_get_colouring", "fsi_solid_get_levels", "fsi_solid_last_error",
     "fsi_solid_launch_count", "fsi_solid_kernel_timing", "fsi_dots_static",
     "fsi_mlp_create", "fsi_mlp_destroy", "fsi_mlp_num_params", "fsi_mlp_params", "fsi_mlp_forward",
-    "fsi_mlp_train_step", "fsi_solid_newmark_advance",
+    "fsi_mlp_train_step", "fsi_solid_newmark_advance", "fsi_dn_default_opts", "fsi_solid_dn_solve",
 ]
 
 # kernel classes of fsi_solid_kernel_timing (FSI_KC_* in the header)
@@ -52,12 +52,13 @@ class MaterialDesc(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
                 ("max_krylov", C.c_int32), ("max_newton", C.c_int32), ("smoother", C.c_int32),
-                ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("cheb_degree", C.c_int32),
+                ("nu_pre", C.c_int32), ("nu_post", C.c_int32),
                 ("coarse_max_nodes", C.c_int32), ("max_levels", C.c_int32), ("use_pspg", C.c_int32),
                 ("adaptive_tol", C.c_int32), ("use_graphs", C.c_int32), ("nu_coarse", C.c_int32),
                 ("omega", C.c_double), ("newton_rtol", C.c_double), ("krylov_rtol", C.c_double),
                 ("fibre_factor", C.c_double), ("inertia_coef", C.c_double), ("amg_lag", C.c_int32),
-                ("assembly", C.c_int32)]
+                ("assembly", C.c_int32), ("precond", C.c_int32), ("schur_theta", C.c_double),
+                ("vanka_omega", C.c_double)]
 
 
 class LoadDesc(C.Structure):
@@ -69,6 +70,20 @@ class Info(C.Structure):
     _fields_ = [("newton_its", C.c_int32), ("krylov_its_total", C.c_int32), ("krylov_its_last", C.c_int32),
                 ("status", C.c_int32), ("guess_accepted", C.c_int32), ("n_levels", C.c_int32),
                 ("res0", C.c_double), ("res", C.c_double), ("inc_norm", C.c_double), ("lin_res", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DnOpts(C.Structure):
+    _fields_ = [("p0", C.c_double), ("added_mass", C.c_double), ("d_ref", C.c_void_p), ("omega0", C.c_double),
+                ("tol", C.c_double), ("max_cycles", C.c_int32), ("aitken", C.c_int32)]
+
+
+class DnInfo(C.Structure):
+    _fields_ = [("cycles", C.c_int32), ("converged", C.c_int32), ("newton_its_total", C.c_int32),
+                ("krylov_its_total", C.c_int32), ("n_interface", C.c_int32), ("res_first", C.c_double),
+                ("res_last", C.c_double), ("omega_last", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,6 +141,10 @@ def _load_library():
     lib.fsi_mlp_train_step.restype = i32
     lib.fsi_solid_newmark_advance.argtypes = [vp, vp, vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, vp]
     lib.fsi_solid_newmark_advance.restype = i32
+    lib.fsi_dn_default_opts.argtypes = [C.POINTER(DnOpts)]
+    lib.fsi_dn_default_opts.restype = None
+    lib.fsi_solid_dn_solve.argtypes = [vp, vp, C.POINTER(LoadDesc), C.POINTER(DnOpts), C.POINTER(DnInfo), vp]
+    lib.fsi_solid_dn_solve.restype = i32
     return lib
 
 
@@ -301,6 +320,25 @@ class SolidSolver:
         self._check(lib.fsi_solid_newmark_advance(self.h, _dev_ptr(state), _dev_ptr(disp), _dev_ptr(vel),
                                                   _dev_ptr(acc), _dev_ptr(hist), float(beta), float(gamma),
                                                   float(dt), _stream()))
+
+    def dn_solve(self, state, p0, added_mass, d_ref=None, load: Optional[Load] = None, check=True, **kw):
+        """Dirichlet-Neumann coupling loop with Aitken relaxation around the solid
+        solve, with the surrogate added-mass fluid map (see the header).  kw:
+        omega0, tol, max_cycles, aitken."""
+        o = DnOpts()
+        lib.fsi_dn_default_opts(C.byref(o))
+        o.p0, o.added_mass = float(p0), float(added_mass)
+        o.d_ref = None if d_ref is None else _dev_ptr(d_ref)
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown DN option {k}")
+            setattr(o, k, v)
+        info = DnInfo()
+        ld = (load or Load()).desc()
+        st = lib.fsi_solid_dn_solve(self.h, _dev_ptr(state), C.byref(ld), C.byref(o), C.byref(info), _stream())
+        if check:
+            self._check(st)
+        return info
 
     def kernel_timing(self, enable: bool):
         """Per-class device time (ms) and launch counts since the last call;

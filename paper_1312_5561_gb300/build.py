@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 BUILD_DIR = os.path.join(ROOT, "_build", "fsi_solid")
 LIB_NAME = "libfsi_solid.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cpp", "amg_setup.cpp", "element.cu", "linalg.cu", "solver.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["setup.cpp", "amg_setup.cpp", "element.cu", "linalg.cu", "solver.cu", "noalloc.cu", "mlp.cu", "coupling.cu", "vanka.cu"]
 
 
 def nvcc_path() -> str:

@@ -616,7 +616,7 @@ void launch_assemble(Handle& h, const double* state, const double* hist, double*
 void launch_assemble_gather(Handle& h, const double* state, const double* hist, double* residual, bool want_tangent,
                             cudaStream_t s, void* vals_target, int target_fp32) {
   Level& L0 = h.levels[0];
-  void* vals = vals_target ? vals_target : L0.vals;
+  void* vals = vals_target ? vals_target : h.k_vals;
   const bool f32 = vals_target ? (target_fp32 == 1) : (h.precision == FSI_PREC_FP32_IR);
   const int ne = h.n_elems;
   const int nbk = blocks_for(ne, kThreads);
@@ -657,7 +657,7 @@ void launch_assemble_gather(Handle& h, const double* state, const double* hist, 
 void launch_assemble_colour(Handle& h, const double* state, const double* hist, double* residual, bool want_tangent,
                             cudaStream_t s, void* vals_target, int target_fp32) {
   Level& L0 = h.levels[0];
-  void* vals = vals_target ? vals_target : L0.vals;
+  void* vals = vals_target ? vals_target : h.k_vals;
   const bool f32 = vals_target ? (target_fp32 == 1) : (h.precision == FSI_PREC_FP32_IR);
   if (residual)
     FSI_LAUNCH(fsi::KC_OTHER, s, init_residual_kernel<<<blocks_for(h.n_nodes, 256), 256, 0, s>>>(h.n_nodes, h.d_fext, residual));

@@ -196,6 +196,25 @@ struct Handle {
   double* d_state_tmp = nullptr; // [ndof]
   double* d_res = nullptr;       // [ndof]
   int red_blocks = 0;
+  // the assembled tangent K.  With the AMG preconditioner on K it is level 0's
+  // value array; with the block-triangular P_L level 0 holds the displacement
+  // block A (u-p couplings removed, identity pressure rows) and K lives here
+  void* k_vals = nullptr;
+  double* d_sinv = nullptr;      // [n_nodes] 1 / S~_ii of Eq. lpreschur (-1 on constrained p)
+  double* d_pl_y = nullptr;      // [ndof] K x_u scratch of P_L
+  // Dirichlet-Neumann coupling: interface Gamma^0 = vertices of the loaded faces
+  int n_gam = 0;
+  int32_t* d_gam_idx = nullptr;  // [n_gam] node ids (ascending)
+  double* d_gam_w = nullptr;     // [n_gam][3] unit direction of the load of a unit pressure
+  double* d_dn = nullptr;        // 5 x [3 n_gam]: d, d~, r, r_prev, dr (r_prev, dr adjacent)
+  double* d_dn_p = nullptr;      // [n_nodes] nodal fluid pressure (zero off Gamma^0)
+  // Vanka smoother of the finest level (smoother == FSI_SMOOTHER_VANKA)
+  int vk_ncol = 0;
+  std::vector<int32_t> vk_cptr;  // colour ranges into d_vk_order
+  int32_t* d_vk_order = nullptr; // [n_nodes] patch centres, colour-major
+  int vk_m = 0;                  // max local unknowns (3 x max row length + 1)
+  void* d_vk_inv = nullptr;      // T [n_nodes][vk_m][vk_m] inverses of the local matrices
+  void* d_vk_z = nullptr;        // T [n_nodes][vk_m] local corrections
 
   cudaStream_t stream = nullptr;
   cudaGraphExec_t vc_exec = nullptr;   // captured V-cycle (use_graphs)
@@ -225,11 +244,20 @@ void launch_newmark(Handle& h, const double* state, double* disp, double* vel, d
 // linalg.cu
 template <typename T>
 void launch_spmv(const Level& L, const T* x, T* y, cudaStream_t s);
-void launch_spmv_f64acc(const Level& L, const double* x, double* y, bool fp32vals, cudaStream_t s);
+// the three operator products take the value array explicitly (level 0's
+// pattern with the values of K, which differ from L.vals under P_L)
+void launch_spmv_f64acc(const Level& L, const void* vals, const double* x, double* y, bool fp32vals, cudaStream_t s);
 // FP32 values with FP64 vectors in double-float arithmetic; y = A x (b == nullptr) or y = b - A x
-void launch_spmv_df(const Level& L, const double* x, float2* xs, const double* b, double* y, cudaStream_t s);
-void launch_residual_f64(const Level& L, const double* b, const double* x, double* r, bool fp32vals,
-                         cudaStream_t s);
+void launch_spmv_df(const Level& L, const void* vals, const double* x, float2* xs, const double* b, double* y,
+                    cudaStream_t s);
+void launch_residual_f64(const Level& L, const void* vals, const double* b, const double* x, double* r,
+                         bool fp32vals, cudaStream_t s);
+// P_L: level-0 values of A from K (u-p couplings dropped, pressure rows identity)
+void launch_split_a(const Level& L, const void* k_vals, bool fp32, cudaStream_t s);
+// P_L stages: b = (r_u, 0) in T; z = (x_u, 0) in FP64; z_p = (y_p - r_p) sinv
+void pl_stage(const double* r, void* b, bool fp32, long n_nodes, cudaStream_t s);
+void pl_unstage(const void* x, double* z, bool fp32, long n_nodes, cudaStream_t s);
+void pl_pressure(const double* y, const double* r, const double* sinv, double* z, long n_nodes, cudaStream_t s);
 void launch_block_inverse(Level& L, bool fp32, int* err, cudaStream_t s);
 // numeric set-up of level+1 from level (smoothed P, P^T, A P, P^T A P)
 void launch_galerkin(Level& L, Level& C, bool fp32, bool filter, cudaStream_t s);
@@ -247,6 +275,20 @@ void scale_copy(double a, const double* x, double* y, long n, cudaStream_t s);
 void to_float(const double* x, float* y, long n, cudaStream_t s);
 void to_double(const float* x, double* y, long n, cudaStream_t s);
 void mask_vector(const uint8_t* cmask, double* x, long n, cudaStream_t s);
+// Vanka smoother (vanka.cu)
+constexpr int kVankaMaxM = 64;   // local unknowns per patch (3 x 21 nodes + 1)
+void vanka_colouring(const HostPattern& pat, int n, std::vector<int32_t>& order, std::vector<int32_t>& cptr,
+                     int* max_deg);
+void launch_vanka_factor(Handle& h, bool fp32, cudaStream_t s);
+template <typename T>
+void vanka_smooth(Handle& h, int sweeps, bool zero_start, cudaStream_t s);
+// Dirichlet-Neumann coupling (coupling.cu)
+void dn_fluid(int ng, const int32_t* idx, const double* w, const double* d, const double* dref, double p0, double c,
+              double* node_p, cudaStream_t s);
+void dn_restrict(int ng, const int32_t* idx, const double* state, double* out, const double* d, double* r,
+                 cudaStream_t s);
+void dn_relax(long m, double omega, const double* dt, double* d, cudaStream_t s);
+void dn_diff(long m, const double* r, const double* r_prev, double* dr, cudaStream_t s);
 // independent segments (batched meshes)
 void segment_sumsq(const int32_t* seg_ptr, int n_seg, const double* x, double* out, cudaStream_t s);
 void segment_normalise(int n_seg, double* a, double* b, cudaStream_t s);

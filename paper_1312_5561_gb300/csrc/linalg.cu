@@ -217,6 +217,53 @@ __global__ void bsr_df_kernel(int n, const int32_t* __restrict__ row_ptr, const 
     y[o] = b[o] - acc;
 }
 
+// Small coarse levels have few but long block rows (~50-110 blocks): one CTA
+// of 32 slots x 7 rows per block row, slot partial sums added in slot order.
+template <typename TV, typename TX, typename TA, int C, int MODE>
+__global__ void __launch_bounds__(224) bsr7_cta_kernel(int n, const int32_t* __restrict__ row_ptr,
+                                                       const int32_t* __restrict__ col_idx,
+                                                       const TV* __restrict__ vals, const TX* __restrict__ x,
+                                                       const TX* __restrict__ b, const TV* __restrict__ dinv,
+                                                       TA omega, TX* __restrict__ y) {
+  constexpr int R = 7, SLOTS = 32;
+  __shared__ TA part[SLOTS][R];
+  __shared__ TA rowsum[R];
+  const int row = blockIdx.x;
+  const int t = threadIdx.x, j = t / R, r = t % R;
+  TA acc = 0;
+  const int k1 = row_ptr[row + 1];
+  for (int k = row_ptr[row] + j; k < k1; k += SLOTS) {
+    const TV* a = vals + (size_t)k * (R * C) + r * C;
+    const TX* xv = x + (size_t)col_idx[k] * C;
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc += (TA)a[c] * (TA)xv[c];
+  }
+  part[j][r] = acc;
+  __syncthreads();
+  if (t < R) {
+    TA s = 0;
+    for (int q = 0; q < SLOTS; ++q) s += part[q][t];
+    rowsum[t] = s;
+  }
+  __syncthreads();
+  if (t >= R) return;
+  const size_t o = (size_t)row * R + t;
+  if constexpr (MODE == 0) {
+    y[o] = (TX)rowsum[t];
+  } else if constexpr (MODE == 1) {
+    y[o] = (TX)((TA)b[o] - rowsum[t]);
+  } else if constexpr (MODE == 3) {
+    y[o] = (TX)((TA)y[o] + rowsum[t]);
+  } else {
+    static_assert(C == R, "Jacobi sweep needs square blocks");
+    const TV* d = dinv + (size_t)row * (R * R) + t * R;
+    TA corr = 0;
+#pragma unroll
+    for (int c = 0; c < R; ++c) corr += (TA)d[c] * ((TA)b[(size_t)row * R + c] - rowsum[c]);
+    y[o] = (TX)((TA)x[o] + omega * corr);
+  }
+}
+
 // x = omega D^-1 b (first Jacobi sweep from a zero guess), B x B blocks
 template <typename T, int B>
 __global__ void jacobi_zero_kernel(int n, const T* __restrict__ dinv, const T* __restrict__ b, T omega,
@@ -334,40 +381,77 @@ __global__ void galerkin_pt_kernel(int p_nb, const int32_t* __restrict__ pt_src,
   pt_v[(size_t)u * (B * NS) + e] = p_v[(size_t)pt_src[u] * (B * NS) + c * NS + r];
 }
 
-// AP[r] = sum over the plan of A_k P_q   (B x B times B x 7)
+// One thread per output block (all B x 7 entries in registers): every pair's
+// two blocks are read once per output block instead of once per entry.
 template <typename T, int B>
-__global__ void galerkin_ap_kernel(int ap_nb, const int32_t* __restrict__ ap_ptr, const int32_t* __restrict__ pairs,
-                                   const T* __restrict__ a_v, const T* __restrict__ p_v, T* __restrict__ ap_v) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int o = (int)(t / (B * NS)), e = (int)(t % (B * NS));
+__global__ void __launch_bounds__(128) galerkin_ap_block_kernel(int ap_nb, const int32_t* __restrict__ ap_ptr,
+                                                                const int32_t* __restrict__ pairs,
+                                                                const T* __restrict__ a_v, const T* __restrict__ p_v,
+                                                                T* __restrict__ ap_v) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= ap_nb) return;
-  const int r = e / NS, c = e % NS;
-  T acc = 0;
-  for (int s = ap_ptr[o]; s < ap_ptr[o + 1]; ++s) {
-    const T* a = a_v + (size_t)pairs[2 * s] * (B * B) + r * B;
-    const T* p = p_v + (size_t)pairs[2 * s + 1] * (B * NS) + c;
+  T acc[B][NS];
 #pragma unroll
-    for (int m = 0; m < B; ++m) acc += a[m] * p[m * NS];
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < NS; ++c) acc[r][c] = 0;
+  for (int s = ap_ptr[o]; s < ap_ptr[o + 1]; ++s) {
+    const T* a = a_v + (size_t)pairs[2 * s] * (B * B);
+    const T* p = p_v + (size_t)pairs[2 * s + 1] * (B * NS);
+    T pv[B][NS];
+#pragma unroll
+    for (int m = 0; m < B; ++m)
+#pragma unroll
+      for (int c = 0; c < NS; ++c) pv[m][c] = p[m * NS + c];
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+#pragma unroll
+      for (int m = 0; m < B; ++m) {
+        const T ar = a[r * B + m];
+#pragma unroll
+        for (int c = 0; c < NS; ++c) acc[r][c] += ar * pv[m][c];
+      }
   }
-  ap_v[(size_t)o * (B * NS) + e] = acc;
+  T* out = ap_v + (size_t)o * (B * NS);
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < NS; ++c) out[r * NS + c] = acc[r][c];
 }
 
-// Ac[o] = sum over the plan of P_q^T AP_r   (7 x B times B x 7)
 template <typename T, int B>
-__global__ void galerkin_ac_kernel(int ac_nb, const int32_t* __restrict__ ac_ptr, const int32_t* __restrict__ pairs,
-                                   const T* __restrict__ p_v, const T* __restrict__ ap_v, T* __restrict__ c_v) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int o = (int)(t / (NS * NS)), e = (int)(t % (NS * NS));
+__global__ void __launch_bounds__(128) galerkin_ac_block_kernel(int ac_nb, const int32_t* __restrict__ ac_ptr,
+                                                                const int32_t* __restrict__ pairs,
+                                                                const T* __restrict__ p_v, const T* __restrict__ ap_v,
+                                                                T* __restrict__ c_v) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= ac_nb) return;
-  const int r = e / NS, c = e % NS;
-  T acc = 0;
-  for (int s = ac_ptr[o]; s < ac_ptr[o + 1]; ++s) {
-    const T* p = p_v + (size_t)pairs[2 * s] * (B * NS) + r;
-    const T* ap = ap_v + (size_t)pairs[2 * s + 1] * (B * NS) + c;
+  T acc[NS][NS];
 #pragma unroll
-    for (int m = 0; m < B; ++m) acc += p[m * NS] * ap[m * NS];
+  for (int r = 0; r < NS; ++r)
+#pragma unroll
+    for (int c = 0; c < NS; ++c) acc[r][c] = 0;
+  for (int s = ac_ptr[o]; s < ac_ptr[o + 1]; ++s) {
+    const T* p = p_v + (size_t)pairs[2 * s] * (B * NS);
+    const T* ap = ap_v + (size_t)pairs[2 * s + 1] * (B * NS);
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      T apm[NS];
+#pragma unroll
+      for (int c = 0; c < NS; ++c) apm[c] = ap[m * NS + c];
+#pragma unroll
+      for (int r = 0; r < NS; ++r) {
+        const T pr = p[m * NS + r];
+#pragma unroll
+        for (int c = 0; c < NS; ++c) acc[r][c] += pr * apm[c];
+      }
+    }
   }
-  c_v[(size_t)o * (NS * NS) + e] = acc;
+  T* out = c_v + (size_t)o * (NS * NS);
+#pragma unroll
+  for (int r = 0; r < NS; ++r)
+#pragma unroll
+    for (int c = 0; c < NS; ++c) out[r * NS + c] = acc[r][c];
 }
 
 template <typename T>
@@ -606,8 +690,12 @@ static void bsr_launch(int n, const int32_t* rp, const int32_t* ci, const void* 
                        const void* dinv, TA omega, TX* y, cudaStream_t s, int cls) {
   if constexpr (R == 7) {
     if (n == 0) return;
-    FSI_LAUNCH(cls, s, bsr7_kernel<TV, TX, TA, C, MODE><<<blocks_for((long)n * 32, 128), 128, 0, s>>>(
-        n, rp, ci, (const TV*)vals, x, b, (const TV*)dinv, omega, y));
+    if (n < 4096)
+      FSI_LAUNCH(cls, s, bsr7_cta_kernel<TV, TX, TA, C, MODE><<<n, 224, 0, s>>>(
+          n, rp, ci, (const TV*)vals, x, b, (const TV*)dinv, omega, y));
+    else
+      FSI_LAUNCH(cls, s, bsr7_kernel<TV, TX, TA, C, MODE><<<blocks_for((long)n * 32, 128), 128, 0, s>>>(
+          n, rp, ci, (const TV*)vals, x, b, (const TV*)dinv, omega, y));
     return;
   }
   constexpr int LN = Lanes<R>::v;
@@ -633,32 +721,97 @@ void split_df(const double* x, float2* xs, long n, cudaStream_t s) {
 }
 
 // FP32 values, FP64 vectors: double-float accumulation (xs is scratch of 4 n float2)
-void launch_spmv_df(const Level& L, const double* x, float2* xs, const double* b, double* y, cudaStream_t s) {
+void launch_spmv_df(const Level& L, const void* vals, const double* x, float2* xs, const double* b, double* y,
+                    cudaStream_t s) {
   split_df(x, xs, 4L * L.n, s);
   if (b)
     FSI_LAUNCH(fsi::KC_BSR0, s, bsr_df_kernel<1><<<blocks_for(4L * L.n, 128), 128, 0, s>>>(
-        L.n, L.row_ptr, L.col_idx, (const float*)L.vals, xs, b, y));
+        L.n, L.row_ptr, L.col_idx, (const float*)vals, xs, b, y));
   else
     FSI_LAUNCH(fsi::KC_BSR0, s, bsr_df_kernel<0><<<blocks_for(4L * L.n, 128), 128, 0, s>>>(
-        L.n, L.row_ptr, L.col_idx, (const float*)L.vals, xs, nullptr, y));
+        L.n, L.row_ptr, L.col_idx, (const float*)vals, xs, nullptr, y));
   FSI_CUDA_TRY(cudaGetLastError());
 }
 
-void launch_spmv_f64acc(const Level& L, const double* x, double* y, bool fp32vals, cudaStream_t s) {
+void launch_spmv_f64acc(const Level& L, const void* vals, const double* x, double* y, bool fp32vals, cudaStream_t s) {
   if (fp32vals)
-    bsr_launch<float, double, double, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, 0.0, y, s, fsi::KC_BSR0);
+    bsr_launch<float, double, double, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, vals, x, nullptr, nullptr, 0.0, y, s, fsi::KC_BSR0);
   else
-    bsr_launch<double, double, double, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, 0.0, y, s, fsi::KC_BSR0);
+    bsr_launch<double, double, double, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, vals, x, nullptr, nullptr, 0.0, y, s, fsi::KC_BSR0);
   FSI_CUDA_TRY(cudaGetLastError());
 }
 
-void launch_residual_f64(const Level& L, const double* b, const double* x, double* r, bool fp32vals,
-                         cudaStream_t s) {
+void launch_residual_f64(const Level& L, const void* vals, const double* b, const double* x, double* r,
+                         bool fp32vals, cudaStream_t s) {
   if (fp32vals)
-    bsr_launch<float, double, double, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, x, b, nullptr, 0.0, r, s, fsi::KC_BSR0);
+    bsr_launch<float, double, double, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, vals, x, b, nullptr, 0.0, r, s, fsi::KC_BSR0);
   else
-    bsr_launch<double, double, double, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, x, b, nullptr, 0.0, r, s, fsi::KC_BSR0);
+    bsr_launch<double, double, double, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, vals, x, b, nullptr, 0.0, r, s, fsi::KC_BSR0);
   FSI_CUDA_TRY(cudaGetLastError());
+}
+
+// ---- block lower-triangular preconditioner P_L (Sec. 4.4.2, Eq. lpre)
+// A from K: one thread per block entry.  Entries coupling u and p are dropped;
+// the pressure row of a diagonal block becomes (0 0 0 1), of any other block 0.
+template <typename T>
+__global__ void split_a_kernel(int nb, const int32_t* __restrict__ brow, const int32_t* __restrict__ col,
+                               const T* __restrict__ k, T* __restrict__ a) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 16L * nb) return;
+  const int blk = (int)(q >> 4), i = (int)(q >> 2) & 3, j = (int)q & 3;
+  T v = k[q];
+  if ((i == 3) != (j == 3)) v = T(0);
+  if (i == 3 && j == 3) v = brow[blk] == col[blk] ? T(1) : T(0);
+  a[q] = v;
+}
+
+void launch_split_a(const Level& L, const void* k_vals, bool fp32, cudaStream_t s) {
+  const int nbk = blocks_for(16L * L.nb, 256);
+  if (fp32)
+    FSI_LAUNCH(fsi::KC_OTHER, s, split_a_kernel<float><<<nbk, 256, 0, s>>>(L.nb, L.block_row, L.col_idx,
+                                                                           (const float*)k_vals, (float*)L.vals));
+  else
+    FSI_LAUNCH(fsi::KC_OTHER, s, split_a_kernel<double><<<nbk, 256, 0, s>>>(L.nb, L.block_row, L.col_idx,
+                                                                            (const double*)k_vals, (double*)L.vals));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+template <typename T>
+__global__ void pl_stage_kernel(long n4, const double* __restrict__ r, T* __restrict__ b) {
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (long)gridDim.x * blockDim.x)
+    b[q] = (q & 3) == 3 ? T(0) : T(r[q]);
+}
+
+template <typename T>
+__global__ void pl_unstage_kernel(long n4, const T* __restrict__ x, double* __restrict__ z) {
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (long)gridDim.x * blockDim.x)
+    z[q] = (q & 3) == 3 ? 0.0 : (double)x[q];
+}
+
+__global__ void pl_pressure_kernel(long nn, const double* __restrict__ y, const double* __restrict__ r,
+                                   const double* __restrict__ sinv, double* __restrict__ z) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x)
+    z[4 * i + 3] = (y[4 * i + 3] - r[4 * i + 3]) * sinv[i];
+}
+
+void pl_stage(const double* r, void* b, bool fp32, long n_nodes, cudaStream_t s) {
+  const long n4 = 4 * n_nodes;
+  if (fp32)
+    FSI_LAUNCH(fsi::KC_VECTOR, s, pl_stage_kernel<float><<<grid_stride_blocks(n4), 256, 0, s>>>(n4, r, (float*)b));
+  else
+    FSI_LAUNCH(fsi::KC_VECTOR, s, pl_stage_kernel<double><<<grid_stride_blocks(n4), 256, 0, s>>>(n4, r, (double*)b));
+}
+
+void pl_unstage(const void* x, double* z, bool fp32, long n_nodes, cudaStream_t s) {
+  const long n4 = 4 * n_nodes;
+  if (fp32)
+    FSI_LAUNCH(fsi::KC_VECTOR, s, pl_unstage_kernel<float><<<grid_stride_blocks(n4), 256, 0, s>>>(n4, (const float*)x, z));
+  else
+    FSI_LAUNCH(fsi::KC_VECTOR, s, pl_unstage_kernel<double><<<grid_stride_blocks(n4), 256, 0, s>>>(n4, (const double*)x, z));
+}
+
+void pl_pressure(const double* y, const double* r, const double* sinv, double* z, long n_nodes, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, pl_pressure_kernel<<<grid_stride_blocks(n_nodes), 256, 0, s>>>(n_nodes, y, r, sinv, z));
 }
 
 template <typename T>
@@ -697,9 +850,9 @@ static void galerkin_t(Level& L, Level& C, bool filter, cudaStream_t s) {
                                                               dsm, (const T*)L.ptent, (const T*)L.w_v,
                                                               (T)L.omega_p, (T*)L.p_v));
   FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_pt_kernel<T, B><<<blocks_for(pe, 256), 256, 0, s>>>(L.p_nb, L.pt_src, (const T*)L.p_v, (T*)L.pt_v));
-  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_kernel<T, B><<<blocks_for((long)L.ap_nb * B * NS, 256), 256, 0, s>>>(
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_block_kernel<T, B><<<blocks_for(L.ap_nb, 128), 128, 0, s>>>(
       L.ap_nb, L.ap_ptr, L.ap_pairs, (const T*)L.vals, (const T*)L.p_v, (T*)L.ap_v));
-  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ac_kernel<T, B><<<blocks_for((long)C.nb * NS * NS, 256), 256, 0, s>>>(
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ac_block_kernel<T, B><<<blocks_for(C.nb, 128), 128, 0, s>>>(
       C.nb, L.ac_ptr, L.ac_pairs, (const T*)L.p_v, (const T*)L.ap_v, (T*)C.vals));
   if (L.n_fix > 0)
     FSI_LAUNCH(fsi::KC_GALERKIN, s, identity_fix_kernel<T><<<blocks_for(L.n_fix, 128), 128, 0, s>>>(L.n_fix, L.fix_blk, L.fix_dof, (T*)C.vals));
@@ -773,7 +926,11 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
   Level& Lc = h.levels[level + 1];
   const int nu_pre = level == 0 ? h.opts.nu_pre : h.opts.nu_coarse;
   const int nu_post = level == 0 ? h.opts.nu_post : h.opts.nu_coarse;
-  smooth<T>(L, omega, nu_pre, true, s);
+  const bool vanka = level == 0 && h.opts.smoother == FSI_SMOOTHER_VANKA;
+  if (vanka)
+    vanka_smooth<T>(h, nu_pre, true, s);
+  else
+    smooth<T>(L, omega, nu_pre, true, s);
   if (L.bs == 4) {
     bsr_launch<T, T, T, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
                                  (T*)L.r, s, fsi::KC_BSR0);
@@ -788,7 +945,10 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
     bsr_launch<T, T, T, 4, 7, 3>(L.n, L.p_rp, L.p_ci, L.p_v, (const T*)Lc.x, nullptr, nullptr, T(0), (T*)L.x, s, fsi::KC_TRANSFER);
   else
     bsr_launch<T, T, T, 7, 7, 3>(L.n, L.p_rp, L.p_ci, L.p_v, (const T*)Lc.x, nullptr, nullptr, T(0), (T*)L.x, s, fsi::KC_TRANSFER);
-  smooth<T>(L, omega, nu_post, false, s);
+  if (vanka)
+    vanka_smooth<T>(h, nu_post, false, s);
+  else
+    smooth<T>(L, omega, nu_post, false, s);
   FSI_CUDA_TRY(cudaGetLastError());
 }
 template void vcycle<double>(Handle&, int, cudaStream_t);

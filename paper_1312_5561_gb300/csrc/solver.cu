@@ -171,6 +171,18 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
   cudaFree(zero);
   cudaFree(kref);
   if (check_err(h, s) & 1) throw ArgError("reference configuration has an inverted element");
+  if (h.opts.precond == FSI_PRECOND_BLOCK_LT) {
+    // P_L: the hierarchy is built for the displacement block A alone (same
+    // transformation as launch_split_a)
+    for (int i = 0; i < A0.n; ++i)
+      for (int q = A0.rp[i]; q < A0.rp[i + 1]; ++q)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            double& v = A0.v[16 * (size_t)q + 4 * a + b];
+            if ((a == 3) != (b == 3)) v = 0.0;
+            if (a == 3 && b == 3) v = A0.ci[q] == i ? 1.0 : 0.0;
+          }
+  }
 
   std::vector<HostLevel> hl;
   HostCoarse hc;
@@ -247,7 +259,9 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
 void amg_numeric(Handle& h, cudaStream_t s) {
   const bool f32 = h.precision == FSI_PREC_FP32_IR;
   const int nl = (int)h.levels.size();
+  if (h.opts.precond == FSI_PRECOND_BLOCK_LT) launch_split_a(h.levels[0], h.k_vals, f32, s);
   launch_block_inverse(h.levels[0], f32, h.d_err, s);
+  if (h.opts.smoother == FSI_SMOOTHER_VANKA) launch_vanka_factor(h, f32, s);
   const bool refresh = h.opts.amg_lag <= 0 || (h.amg_calls % (h.opts.amg_lag + 1)) == 0;
   ++h.amg_calls;
   if (!refresh) return;
@@ -290,8 +304,26 @@ void run_vcycle(Handle& h, cudaStream_t s) {
   g_launches += h.vc_kernels;
 }
 
-// z = M^-1 v (one V-cycle)
+void apply_operator(Handle& h, const double* x, double* y, cudaStream_t s);
+
+// z = P_L^-1 v (Eq. lpre): z_u = one V-cycle on A applied to v_u, then
+// z_p = S~^-1 (B2 z_u - v_p); B2 z_u is the pressure part of K (z_u, 0)
+static void precondition_pl(Handle& h, const double* v, double* z, cudaStream_t s) {
+  Level& L0 = h.levels[0];
+  const bool f32 = h.precision == FSI_PREC_FP32_IR;
+  pl_stage(v, L0.b, f32, L0.n, s);
+  run_vcycle(h, s);
+  pl_unstage(L0.x, z, f32, L0.n, s);
+  apply_operator(h, z, h.d_pl_y, s);
+  pl_pressure(h.d_pl_y, v, h.d_sinv, z, L0.n, s);
+}
+
+// z = M^-1 v (one V-cycle, or P_L)
 void precondition(Handle& h, const double* v, double* z, cudaStream_t s) {
+  if (h.opts.precond == FSI_PRECOND_BLOCK_LT) {
+    precondition_pl(h, v, z, s);
+    return;
+  }
   Level& L0 = h.levels[0];
   const long n = 4L * L0.n;
   if (h.precision == FSI_PREC_FP32_IR) {
@@ -309,16 +341,16 @@ void precondition(Handle& h, const double* v, double* z, cudaStream_t s) {
 // double-float arithmetic; with FP64 values in FP64.
 void apply_operator(Handle& h, const double* x, double* y, cudaStream_t s) {
   if (h.precision == FSI_PREC_FP32_IR)
-    launch_spmv_df(h.levels[0], x, h.d_xdf, nullptr, y, s);
+    launch_spmv_df(h.levels[0], h.k_vals, x, h.d_xdf, nullptr, y, s);
   else
-    launch_spmv_f64acc(h.levels[0], x, y, false, s);
+    launch_spmv_f64acc(h.levels[0], h.k_vals, x, y, false, s);
 }
 
 void operator_residual(Handle& h, const double* b, const double* x, double* r, cudaStream_t s) {
   if (h.precision == FSI_PREC_FP32_IR)
-    launch_spmv_df(h.levels[0], x, h.d_xdf, b, r, s);
+    launch_spmv_df(h.levels[0], h.k_vals, x, h.d_xdf, b, r, s);
   else
-    launch_residual_f64(h.levels[0], b, x, r, false, s);
+    launch_residual_f64(h.levels[0], h.k_vals, b, x, r, false, s);
 }
 
 // FGMRES(m), right preconditioned.  Returns iterations; *rel = ||b - A x|| / ||b||.
@@ -417,17 +449,85 @@ int fgmres(Handle& h, const double* b, double* x, double rtol, int maxit, double
   return total;
 }
 
+// BiCGStab (van der Vorst), right-preconditioned by the same V-cycle: the
+// paper's Krylov method for the solid (Sec. 5.4.2), here with the coupled AMG
+// preconditioner.  Short recurrences: no restart length, two preconditioner
+// and two operator applications per iteration.  Returns iterations.
+int bicgstab(Handle& h, const double* b, double* x, double rtol, int maxit, double* rel, cudaStream_t s) {
+  const long n = 4L * h.n_nodes;
+  double* r = h.d_r;
+  double* r0 = h.d_V;                       // shadow residual
+  double* p = h.d_V + (size_t)n;
+  double* v = h.d_V + 2 * (size_t)n;
+  double* phat = h.d_Z;
+  double* shat = h.d_Z + (size_t)n;
+  double* t = h.d_w;
+  operator_residual(h, b, x, r, s);
+  const double bnorm = norm2_host(h, b, n, s);
+  if (bnorm == 0.0) {
+    FSI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    *rel = 0.0;
+    return 0;
+  }
+  const double target = rtol * bnorm;
+  double rn = norm2_host(h, r, n, s);
+  FSI_CUDA_TRY(cudaMemcpyAsync(r0, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  FSI_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(double) * n, s));
+  FSI_CUDA_TRY(cudaMemsetAsync(v, 0, sizeof(double) * n, s));
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  int it = 0;
+  auto dot = [&](const double* a, const double* bb) {
+    dots(h, a, 0, 1, bb, n, h.d_dots + kDotNorm + 1, s);
+    double v_ = 0.0;
+    FSI_CUDA_TRY(cudaMemcpyAsync(&v_, h.d_dots + kDotNorm + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FSI_CUDA_TRY(cudaStreamSynchronize(s));
+    return v_;
+  };
+  while (rn > target && it < maxit) {
+    const double rho1 = dot(r0, r);
+    if (rho1 == 0.0) break;
+    const double beta = (rho1 / rho) * (alpha / omega);
+    // p = r + beta (p - omega v)
+    axpy(-omega, v, p, n, s);
+    scale_copy(beta, p, p, n, s);
+    axpy(1.0, r, p, n, s);
+    precondition(h, p, phat, s);
+    apply_operator(h, phat, v, s);
+    alpha = rho1 / dot(r0, v);
+    axpy(-alpha, v, r, n, s);                 // r becomes s
+    axpy(alpha, phat, x, n, s);
+    ++it;
+    rn = norm2_host(h, r, n, s);
+    if (rn <= target) break;
+    precondition(h, r, shat, s);
+    apply_operator(h, shat, t, s);
+    const double tt = dot(t, t);
+    omega = tt > 0.0 ? dot(t, r) / tt : 0.0;
+    axpy(omega, shat, x, n, s);
+    axpy(-omega, t, r, n, s);
+    rn = norm2_host(h, r, n, s);
+    rho = rho1;
+    if (omega == 0.0) break;
+  }
+  operator_residual(h, b, x, r, s);           // true residual
+  *rel = norm2_host(h, r, n, s) / bnorm;
+  return it;
+}
+
 void set_error(Handle* h, const std::string& msg) {
   if (h) h->last_error = msg;
 }
 
 int linear_solve(Handle& h, const double* b, double* x, double rtol, double* rel, cudaStream_t s) {
+  if (h.opts.krylov == FSI_KRYLOV_BICGSTAB) return bicgstab(h, b, x, rtol, h.opts.max_krylov, rel, s);
   return fgmres(h, b, x, rtol, h.opts.max_krylov, rel, s);
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ create / destroy
+static void destroy_impl(Handle* hp);
+
 static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_material* mats,
                            const fsi_solver_opts* opts) {
   if (!mesh || !mats || n_mat <= 0) throw ArgError("mesh and material table are required");
@@ -458,10 +558,20 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
     }
 
   Handle* hp = new Handle();
+  // a create that fails part-way releases what it has allocated
+  struct Guard {
+    Handle* p;
+    ~Guard() { if (p) destroy_impl(p); }
+  } guard{hp};
   Handle& h = *hp;
   fsi_solid_default_opts(&h.opts);
   if (opts) h.opts = *opts;
+  if (h.opts.precond != FSI_PRECOND_AMG && h.opts.precond != FSI_PRECOND_BLOCK_LT)
+    throw ArgError("unknown preconditioner");
+  if (h.opts.smoother != FSI_SMOOTHER_JACOBI && h.opts.smoother != FSI_SMOOTHER_VANKA)
+    throw ArgError("unknown smoother");
   h.opts.restart = std::min(std::max(h.opts.restart, 1), kMaxRestart);
+  if (h.opts.krylov == FSI_KRYLOV_BICGSTAB) h.opts.restart = std::max(h.opts.restart, 2);   // BiCGStab work vectors
   h.m = h.opts.restart;
   h.precision = h.opts.precision == FSI_PREC_FP32_IR ? FSI_PREC_FP32_IR : FSI_PREC_FP64;
   const bool f32 = h.precision == FSI_PREC_FP32_IR;
@@ -577,8 +687,46 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
   L0.bs = 4;
   L0.cmask = h.d_dir_mask;
   L0.vals = dalloc<char>((f32 ? 4 : 8) * 16 * (size_t)L0.nb);
+  h.k_vals = L0.vals;
+  if (h.opts.precond == FSI_PRECOND_BLOCK_LT) {
+    h.k_vals = dalloc<char>((f32 ? 4 : 8) * 16 * (size_t)L0.nb);
+    // S~ = (1/theta + 1/kappa) diag(M_p), M_aa = V/10 per incident tetrahedron
+    const double theta = h.opts.schur_theta > 0.0 ? h.opts.schur_theta : mats[0].c10;
+    if (!(theta > 0.0)) throw ArgError("schur_theta must be positive (or c10 of material 0)");
+    std::vector<double> sd(nn, 0.0);
+    for (int e = 0; e < ne; ++e) {
+      const int32_t* t = mesh->tets + 4 * (size_t)e;
+      const double* x0 = mesh->X + 3 * (size_t)t[0];
+      double d[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) d[a][c] = mesh->X[3 * (size_t)t[a + 1] + c] - x0[c];
+      const double vol = std::fabs(d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) -
+                                   d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
+                                   d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0])) / 6.0;
+      const double w = (1.0 / theta + 1.0 / mats[mesh->mat_id[e]].kappa) * vol / 10.0;
+      for (int a = 0; a < 4; ++a) sd[t[a]] += w;
+    }
+    std::vector<double> sinv(nn);
+    for (int i = 0; i < nn; ++i) sinv[i] = dmask[4 * (size_t)i + 3] ? -1.0 : (sd[i] > 0.0 ? 1.0 / sd[i] : 0.0);
+    h.d_sinv = upload(sinv, s);
+    h.d_pl_y = dalloc<double>(4 * (size_t)nn);
+    FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   L0.dinv = dalloc<char>((f32 ? 4 : 8) * 16 * (size_t)L0.n);
   alloc_level_vectors(L0, f32);
+  if (h.opts.smoother == FSI_SMOOTHER_VANKA) {
+    std::vector<int32_t> order;
+    int max_deg = 0;
+    vanka_colouring(L0.hpat, nn, order, h.vk_cptr, &max_deg);
+    h.vk_ncol = (int)h.vk_cptr.size() - 1;
+    h.vk_m = 3 * max_deg + 1;
+    if (h.vk_m > kVankaMaxM) throw ArgError("a Vanka patch would exceed 64 unknowns (node with > 20 neighbours)");
+    h.d_vk_order = upload(order, s);
+    const size_t ts = f32 ? 4 : 8;
+    h.d_vk_inv = dalloc<char>(ts * (size_t)nn * h.vk_m * h.vk_m);
+    h.d_vk_z = dalloc<char>(ts * (size_t)nn * h.vk_m);
+    FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   build_hierarchy(h, free0, comp, mesh->X, s);
 
   const size_t ndof = 4 * (size_t)nn;
@@ -594,11 +742,47 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
   h.d_state_tmp = dalloc<double>(ndof);
   h.d_fext = dalloc<double>(3 * (size_t)nn);
   FSI_CUDA_TRY(cudaMemsetAsync(h.d_fext, 0, sizeof(double) * 3 * nn, s));
+  if (mesh->n_faces > 0) {
+    // coupling interface: vertices of the loaded faces, with the unit direction
+    // of the P1 load of a unit pressure (-sum over faces of the doubled area normal)
+    std::vector<double> f(3 * (size_t)nn, 0.0);
+    std::vector<uint8_t> on(nn, 0);
+    for (int q = 0; q < mesh->n_faces; ++q) {
+      const int32_t* v = mesh->neu_faces + 3 * (size_t)q;
+      double e1[3], e2[3];
+      for (int c = 0; c < 3; ++c) {
+        e1[c] = mesh->X[3 * (size_t)v[1] + c] - mesh->X[3 * (size_t)v[0] + c];
+        e2[c] = mesh->X[3 * (size_t)v[2] + c] - mesh->X[3 * (size_t)v[0] + c];
+      }
+      const double nv[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                            e1[0] * e2[1] - e1[1] * e2[0]};
+      for (int a = 0; a < 3; ++a) {
+        on[v[a]] = 1;
+        for (int c = 0; c < 3; ++c) f[3 * (size_t)v[a] + c] -= nv[c];
+      }
+    }
+    std::vector<int32_t> gi;
+    std::vector<double> gw;
+    for (int i = 0; i < nn; ++i) {
+      if (!on[i]) continue;
+      const double* fi = &f[3 * (size_t)i];
+      const double len = std::sqrt(fi[0] * fi[0] + fi[1] * fi[1] + fi[2] * fi[2]);
+      gi.push_back(i);
+      for (int c = 0; c < 3; ++c) gw.push_back(len > 0.0 ? fi[c] / len : 0.0);
+    }
+    h.n_gam = (int)gi.size();
+    h.d_gam_idx = upload(gi, s);
+    h.d_gam_w = upload(gw, s);
+    h.d_dn = dalloc<double>(15 * (size_t)h.n_gam);
+    h.d_dn_p = dalloc<double>(nn);
+    FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   h.red_blocks = 2 * 152;
   h.d_partial = dalloc<double>((size_t)h.red_blocks * (kMaxRestart + 1));
   h.d_dots = dalloc<double>(kDotSize);
   FSI_CUDA_TRY(cudaMallocHost((void**)&h.h_dots, sizeof(double) * kDotSize));
   FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  guard.p = nullptr;
   return hp;
 }
 
@@ -615,6 +799,16 @@ static void destroy_impl(Handle* hp) {
                     (void*)L.ac_pairs, (void*)L.fix_blk, (void*)L.fix_dof})
       dfree(p);
   }
+  if (h.k_vals && !h.levels.empty() && h.k_vals != h.levels[0].vals) dfree(h.k_vals);
+  dfree(h.d_sinv);
+  dfree(h.d_pl_y);
+  dfree(h.d_gam_idx);
+  dfree(h.d_gam_w);
+  dfree(h.d_dn);
+  dfree(h.d_dn_p);
+  dfree(h.d_vk_order);
+  dfree(h.d_vk_inv);
+  dfree(h.d_vk_z);
   for (void* p : {(void*)h.coarse.comp_ptr, (void*)h.coarse.inv_off, h.coarse.inv, (void*)h.coarse.work,
                   (void*)h.d_conn, (void*)h.d_geo, (void*)h.d_fibre, (void*)h.d_mat, (void*)h.d_slot,
                   (void*)h.d_mats, (void*)h.d_X, (void*)h.d_dir_mask, (void*)h.d_faces, (void*)h.d_nf_ptr,
@@ -688,8 +882,10 @@ static void segment_norms(Handle& h, const double* x, std::vector<double>& out, 
   for (int q = 0; q < h.n_seg; ++q) out[q] = std::sqrt(h.h_seg[q]);
 }
 
+// Newton's method for one load (time) step.  The stop is relative to the
+// initial residual norm, or to r_ref when r_ref > 0 (single-segment meshes).
 static int solve_impl(Handle& h, double* state, const fsi_load* load, const double* guess, fsi_info* info,
-                      cudaStream_t s) {
+                      cudaStream_t s, double r_ref = 0.0) {
   const long n = 4L * h.n_nodes;
   fsi_info loc{};
   if (!info) info = &loc;
@@ -721,7 +917,10 @@ static int solve_impl(Handle& h, double* state, const fsi_load* load, const doub
   std::vector<double> seg0, segk;
   if (h.n_seg > 1) segment_norms(h, h.d_res, seg0, s);
   auto converged = [&]() {
-    if (h.n_seg == 1) return r0 == 0.0 || rn <= h.opts.newton_rtol * r0;
+    if (h.n_seg == 1) {
+      const double ref = r_ref > 0.0 ? r_ref : r0;
+      return ref == 0.0 || rn <= h.opts.newton_rtol * ref;
+    }
     segment_norms(h, h.d_res, segk, s);
     for (int q = 0; q < h.n_seg; ++q)
       if (segk[q] > h.opts.newton_rtol * seg0[q]) return false;
@@ -743,6 +942,12 @@ static int solve_impl(Handle& h, double* state, const fsi_load* load, const doub
       return st;
     }
     st = assemble_checked(h, state, hist, h.d_res, false, s);
+    // safeguard (the paper's Newton has none): if the full step inverts an
+    // element, halve it, up to six times; dv is still in d_t2
+    for (int half = 1; st == FSI_ERR_INVERTED && half <= 6; ++half) {
+      axpy(-std::ldexp(1.0, -half), h.d_t2, state, n, s);
+      st = assemble_checked(h, state, hist, h.d_res, false, s);
+    }
     if (st) {
       info->newton_its = k + 1;
       return st;
@@ -754,6 +959,63 @@ static int solve_impl(Handle& h, double* state, const fsi_load* load, const doub
   info->newton_its = k;
   info->res = rn;
   return FSI_OK;
+}
+
+// Dirichlet-Neumann iteration with Aitken relaxation (Sec. 5.1, 5.2).
+static int dn_impl(Handle& h, double* state, const fsi_load* load, const fsi_dn_opts& o, fsi_dn_info* info,
+                   cudaStream_t s) {
+  const int ng = h.n_gam;
+  const long m = 3L * ng;
+  double* d = h.d_dn;
+  double* dt = h.d_dn + m;
+  double* r = h.d_dn + 2 * m;
+  double* r_prev = h.d_dn + 3 * m;   // r_prev and dr adjacent: one dots() call gives both products
+  double* dr = h.d_dn + 4 * m;
+  fsi_load ld{};
+  if (load) ld = *load;
+  ld.pressure = 1.0;
+  ld.node_pressure = h.d_dn_p;
+  ld.face_pressure = nullptr;
+  if (ld.dir_values) {
+    launch_set_dirichlet_values(h, state, ld.dir_values, s);
+    ld.dir_values = nullptr;
+  }
+  FSI_CUDA_TRY(cudaMemsetAsync(h.d_dn_p, 0, sizeof(double) * h.n_nodes, s));
+  dn_restrict(ng, h.d_gam_idx, state, d, nullptr, nullptr, s);     // d_0
+  double omega = o.omega0, r_ref = 0.0;
+  bool have_prev = false;
+  const double scale = 1.0 / std::sqrt((double)ng);
+  for (int k = 1; k <= o.max_cycles; ++k) {
+    dn_fluid(ng, h.d_gam_idx, h.d_gam_w, d, o.d_ref, o.p0, o.added_mass, h.d_dn_p, s);
+    fsi_info ni{};
+    int st = solve_impl(h, state, &ld, nullptr, &ni, s, r_ref);
+    info->newton_its_total += ni.newton_its;
+    info->krylov_its_total += ni.krylov_its_total;
+    info->cycles = k;
+    if (st) return st;
+    if (k == 1) r_ref = ni.res0;
+    dn_restrict(ng, h.d_gam_idx, state, dt, d, r, s);                 // d~_k, r_k
+    const double res = norm2_host(h, r, m, s) * scale;
+    if (k == 1) info->res_first = res;
+    info->res_last = res;
+    if (res < o.tol) {
+      info->converged = 1;
+      return FSI_OK;
+    }
+    if (o.aitken && have_prev) {
+      dn_diff(m, r, r_prev, dr, s);
+      dots(h, r_prev, m, 2, dr, m, h.d_dots + kDotNorm + 1, s);    // r_prev . dr, dr . dr
+      double pr[2];
+      FSI_CUDA_TRY(cudaMemcpyAsync(pr, h.d_dots + kDotNorm + 1, sizeof(pr), cudaMemcpyDeviceToHost, s));
+      FSI_CUDA_TRY(cudaStreamSynchronize(s));
+      if (pr[1] > 0.0) omega = -omega * pr[0] / pr[1];
+    }
+    info->omega_last = omega;
+    dn_relax(m, omega, dt, d, s);
+    FSI_CUDA_TRY(cudaMemcpyAsync(r_prev, r, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    have_prev = true;
+  }
+  return FSI_ERR_NOT_CONVERGED;
 }
 
 }  // namespace fsi
@@ -805,7 +1067,6 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->nu_pre = 4;
   o->nu_post = 4;
   o->nu_coarse = 1;
-  o->cheb_degree = 3;
   o->coarse_max_nodes = 16;
   o->max_levels = 12;
   o->use_pspg = 1;
@@ -817,6 +1078,10 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->krylov_rtol = 1e-8;
   o->fibre_factor = 2.0;
   o->inertia_coef = 0.0;
+  o->assembly = 0;
+  o->precond = FSI_PRECOND_AMG;
+  o->schur_theta = 0.0;
+  o->vanka_omega = 0.86;
 }
 
 fsi_status fsi_solid_create(const fsi_mesh_desc* mesh, int32_t n_mat, const fsi_material* mats,
@@ -872,7 +1137,7 @@ fsi_status fsi_solid_get_bsr(fsi_solid_t hh, const int32_t** row_ptr, const int3
   const fsi::Level& L = h->levels[0];
   if (row_ptr) *row_ptr = L.row_ptr;
   if (col_idx) *col_idx = L.col_idx;
-  if (vals) *vals = L.vals;
+  if (vals) *vals = h->k_vals;
   if (dtype) *dtype = h->precision == FSI_PREC_FP32_IR ? 1 : 0;
   if (n_blocks) *n_blocks = L.nb;
   return FSI_OK;
@@ -951,6 +1216,38 @@ fsi_status fsi_solid_solve(fsi_solid_t hh, double* state, const fsi_load* load, 
   FSI_CUDA_TRY(cudaStreamSynchronize(s));
   if (info) info->status = st;
   if (st) fsi::set_error(h, st == FSI_ERR_INVERTED ? "inverted or non-finite element" : "Newton did not converge");
+  return (fsi_status)st;
+  FSI_GUARD_END(h)
+}
+
+void fsi_dn_default_opts(fsi_dn_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->omega0 = 0.5;
+  o->tol = 1e-8;
+  o->max_cycles = 50;
+  o->aitken = 1;
+}
+
+fsi_status fsi_solid_dn_solve(fsi_solid_t hh, double* state, const fsi_load* load, const fsi_dn_opts* o,
+                              fsi_dn_info* info, void* stream) {
+  Handle* h = H(hh);
+  if (!h || !state || !o) return FSI_ERR_ARG;
+  FSI_GUARD_BEGIN
+  FSI_PROF(h);
+  fsi_dn_info loc{};
+  if (!info) info = &loc;
+  *info = fsi_dn_info{};
+  info->n_interface = h->n_gam;
+  if (h->n_gam == 0) throw fsi::ArgError("no loaded faces: the coupling interface is empty");
+  if (!(o->omega0 > 0.0 && o->omega0 <= 1.0)) throw fsi::ArgError("omega0 must lie in (0, 1]");
+  if (!(o->added_mass >= 0.0)) throw fsi::ArgError("added_mass must be >= 0");
+  if (o->max_cycles < 1) throw fsi::ArgError("max_cycles must be >= 1");
+  cudaStream_t s = S(h, stream);
+  int st = fsi::dn_impl(*h, state, load, *o, info, s);
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  if (st) fsi::set_error(h, st == FSI_ERR_INVERTED ? "inverted or non-finite element"
+                                                     : "DN iteration or Newton did not converge");
   return (fsi_status)st;
   FSI_GUARD_END(h)
 }

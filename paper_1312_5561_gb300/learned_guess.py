@@ -225,10 +225,17 @@ def run_study(mesh, n_steps, n_train, dt=0.01, period=1.0, train_steps=2000, nod
     for name, fn in strategies.items():
         loop.restore(snap)
         its, acc = [], []
-        for _ in range(n_steps - n_train):
-            rec = loop.step(fn)
+        for j in range(n_steps - n_train):
+            try:
+                rec = loop.step(fn)
+            except B.FsiError:
+                if log:
+                    log(f"{name}: solve failed at step {loop.step_index + 1}")
+                raise
             its.append(rec.newton_its)
             acc.append(getattr(rec, "guess_accepted", 0))
+            if log and j % 50 == 0:
+                log(f"{name} step {loop.step_index} newton {rec.newton_its}")
         results[name] = {"mean_newton_its": float(np.mean(its)), "accepted": float(np.mean(acc))}
         if log:
             log(f"{name}: mean Newton its {np.mean(its):.3f} accepted {np.mean(acc):.2f}")

@@ -39,9 +39,11 @@ def test_struct_layouts_match_header():
     import subprocess
     import tempfile
     from paper_1312_5561_gb300 import binding as b
-    code = ('#include "fsi_solid.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(){printf("%zu %zu %zu %zu %zu %zu\\n",'
+    code = ('#include "fsi_solid.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(){printf("%zu %zu %zu %zu %zu %zu '
+            '%zu %zu %zu %zu\\n",'
             'sizeof(fsi_mesh_desc),sizeof(fsi_material),sizeof(fsi_solver_opts),sizeof(fsi_load),sizeof(fsi_info),'
-            'offsetof(fsi_solver_opts, omega));}')
+            'offsetof(fsi_solver_opts, omega),offsetof(fsi_solver_opts, schur_theta),sizeof(fsi_dn_opts),'
+            'sizeof(fsi_dn_info),offsetof(fsi_dn_opts, max_cycles));}')
     with tempfile.TemporaryDirectory() as d:
         src = os.path.join(d, "s.c")
         open(src, "w").write(code)
@@ -49,7 +51,9 @@ def test_struct_layouts_match_header():
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
         sizes = list(map(int, subprocess.check_output([exe]).split()))
     got = [ctypes.sizeof(b.MeshDesc), ctypes.sizeof(b.MaterialDesc), ctypes.sizeof(b.SolverOpts),
-           ctypes.sizeof(b.LoadDesc), ctypes.sizeof(b.Info), b.SolverOpts.omega.offset]
+           ctypes.sizeof(b.LoadDesc), ctypes.sizeof(b.Info), b.SolverOpts.omega.offset,
+           b.SolverOpts.schur_theta.offset, ctypes.sizeof(b.DnOpts), ctypes.sizeof(b.DnInfo),
+           b.DnOpts.max_cycles.offset]
     assert got == sizes
 
 
