@@ -173,6 +173,8 @@ def run_gpu(args, rank, world):
     # fgmres-amg: FGMRES(100) + one AMG V-cycle on the whole u-p tangent;
     # bicgstab-pl: the paper's solid solver, BiCGStab + block-triangular P_L (Sec. 4.4.2)
     kry = dict(krylov=1, precond=1, max_krylov=3000) if args.solver == "bicgstab-pl" else dict(max_krylov=600)
+    if args.coarse_bf16:
+        kry.update(coarse_bf16=1)
     if args.smoother == "vanka":       # the paper's Vanka smoother on the finest level (Sec. 4.5)
         kry.update(smoother=1, vanka_omega=0.86, nu_pre=args.nu, nu_post=args.nu)
     solver = SolidSolver(mesh, precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=int(args.graphs),
@@ -335,6 +337,7 @@ def main():
     ap.add_argument("--solver", default="fgmres-amg", choices=["fgmres-amg", "bicgstab-pl"])
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "vanka"])
     ap.add_argument("--nu", type=int, default=1, help="Vanka sweeps before / after the coarse correction")
+    ap.add_argument("--coarse-bf16", type=int, default=0, help="BF16 coarse-level operators in the V-cycle")
     ap.add_argument("--compare-paper-solver", action="store_true",
                     help="also time BiCGStab + P_L (the paper's solid solver) on the same workload")
     args = ap.parse_args()
@@ -399,6 +402,7 @@ def main():
                                else "FGMRES(100) + AMG V-cycle on K"),
                        finest_smoother=(f"Vanka, {args.nu}+{args.nu} sweeps, omega 0.86" if args.smoother == "vanka"
                                         else "damped block Jacobi, 4+4 sweeps, omega 0.7"),
+                       coarse_operators="BF16 (V-cycle reads)" if args.coarse_bf16 else "FP32",
                        krylov_its_per_step=round(res["krylov_per_step"], 1),
                        krylov_cap_hits_in_timed_steps=res["krylov_cap_hits"], amg_levels=res["levels"]),
         "element_tangents_per_s": res["tangents_per_s"] * world,

@@ -137,6 +137,10 @@ typedef struct {
                                <= 0: c10 of material 0 */
   double vanka_omega;       /* relaxation of the Vanka update (the paper: 0.78 for
                                Mooney-Rivlin, 0.86 for the artery) */
+  int32_t coarse_bf16;      /* FSI_PREC_FP32_IR only: the V-cycle reads the coarse-level
+                               (7x7) operators as BF16 copies (smoothing and residual;
+                               FP32 accumulation); the Galerkin products, transfers,
+                               block inverses and coarsest solve stay FP32 */
 } fsi_solver_opts;
 
 /* Load of one solve (device arrays owned by the caller; NULL = absent).

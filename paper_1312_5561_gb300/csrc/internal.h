@@ -89,6 +89,7 @@ struct Level {
   int32_t* block_row = nullptr;
   void* vals = nullptr;      // T [nb][bs*bs]
   void* dinv = nullptr;      // T [n][bs*bs] inverses of the diagonal blocks
+  void* vals_lp = nullptr;   // BF16 copy of vals read by the V-cycle (coarse levels, FP32 mode, coarse_bf16)
   uint8_t* cmask = nullptr;  // level 0: [n][4] 1 = constrained component
   // prolongation from level+1 (rows: this level's nodes) and restriction (its transpose)
   int p_nb = 0, pt_nb = 0;
@@ -262,6 +263,8 @@ void launch_block_inverse(Level& L, bool fp32, int* err, cudaStream_t s);
 // numeric set-up of level+1 from level (smoothed P, P^T, A P, P^T A P)
 void launch_galerkin(Level& L, Level& C, bool fp32, bool filter, cudaStream_t s);
 void launch_coarse_factor(Handle& h, bool fp32, cudaStream_t s);
+// L.vals_lp = bf16(L.vals) (FP32 values, 7x7 blocks)
+void launch_values_to_bf16(const Level& L, cudaStream_t s);
 template <typename T>
 void vcycle(Handle& h, int level, cudaStream_t s);
 // FP64 vector helpers; reductions are deterministic (fixed two-pass order)

@@ -2,7 +2,10 @@
 // residuals, damped block-Jacobi smoothing, aggregation transfers, Galerkin
 // coarse operators, the block-diagonal dense coarse solve and the FP64
 // vector kernels of the Krylov method (deterministic reductions).
+#include <cuda_bf16.h>
+
 #include <cmath>
+#include <type_traits>
 #include <utility>
 
 #include "internal.h"
@@ -58,7 +61,27 @@ __global__ void bsr_kernel(int n, const int32_t* __restrict__ row_ptr, const int
   TA acc = 0;
   if (active) {
     const int k0 = row_ptr[row], k1 = row_ptr[row + 1];
-    for (int k = k0; k < k1; ++k) {
+    int k = k0;
+    if constexpr (C == 4) {
+      // four blocks per step: all index, value and vector loads are issued
+      // before the products, so each warp keeps four blocks in flight
+      for (; k + 4 <= k1; k += 4) {
+        int j[4];
+        TV v[4][4];
+        TX xx[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) j[u] = col_idx[k + u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) Vec4<TV>::load(vals + (size_t)(k + u) * (R * C) + r * C, v[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) Vec4<TX>::load(x + (size_t)j[u] * C, xx[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          acc += (TA)v[u][0] * (TA)xx[u][0] + (TA)v[u][1] * (TA)xx[u][1] + (TA)v[u][2] * (TA)xx[u][2] +
+                 (TA)v[u][3] * (TA)xx[u][3];
+      }
+    }
+    for (; k < k1; ++k) {
       const int j = col_idx[k];
       const TV* a = vals + (size_t)k * (R * C) + r * C;
       const TX* xv = x + (size_t)j * C;
@@ -103,10 +126,10 @@ __global__ void bsr_kernel(int n, const int32_t* __restrict__ row_ptr, const int
 // every fourth block of the row and row r of each; the four slot sums are
 // then added in a fixed order ((s0 + s2) + (s1 + s3)).  Long coarse rows
 // (~50 blocks) thereby keep 28 lanes busy instead of 7.  Modes as above.
-template <typename TV, typename TX, typename TA, int C, int MODE>
+template <typename TV, typename TX, typename TA, int C, int MODE, typename TD = TV>
 __global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                             const TV* __restrict__ vals, const TX* __restrict__ x, const TX* __restrict__ b,
-                            const TV* __restrict__ dinv, TA omega, TX* __restrict__ y) {
+                            const TD* __restrict__ dinv, TA omega, TX* __restrict__ y) {
   constexpr int R = 7;
   const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -146,7 +169,7 @@ __global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const in
 #pragma unroll
     for (int c = 0; c < R; ++c) rr[c] = __shfl_sync(0xffffffffu, res, c);
     if (out) {
-      const TV* d = dinv + (size_t)row * (R * R) + lane * R;
+      const TD* d = dinv + (size_t)row * (R * R) + lane * R;
       TA corr = 0;
 #pragma unroll
       for (int c = 0; c < R; ++c) corr += (TA)d[c] * rr[c];
@@ -219,11 +242,11 @@ __global__ void bsr_df_kernel(int n, const int32_t* __restrict__ row_ptr, const 
 
 // Small coarse levels have few but long block rows (~50-110 blocks): one CTA
 // of 32 slots x 7 rows per block row, slot partial sums added in slot order.
-template <typename TV, typename TX, typename TA, int C, int MODE>
+template <typename TV, typename TX, typename TA, int C, int MODE, typename TD = TV>
 __global__ void __launch_bounds__(224) bsr7_cta_kernel(int n, const int32_t* __restrict__ row_ptr,
                                                        const int32_t* __restrict__ col_idx,
                                                        const TV* __restrict__ vals, const TX* __restrict__ x,
-                                                       const TX* __restrict__ b, const TV* __restrict__ dinv,
+                                                       const TX* __restrict__ b, const TD* __restrict__ dinv,
                                                        TA omega, TX* __restrict__ y) {
   constexpr int R = 7, SLOTS = 32;
   __shared__ TA part[SLOTS][R];
@@ -256,7 +279,7 @@ __global__ void __launch_bounds__(224) bsr7_cta_kernel(int n, const int32_t* __r
     y[o] = (TX)((TA)y[o] + rowsum[t]);
   } else {
     static_assert(C == R, "Jacobi sweep needs square blocks");
-    const TV* d = dinv + (size_t)row * (R * R) + t * R;
+    const TD* d = dinv + (size_t)row * (R * R) + t * R;
     TA corr = 0;
 #pragma unroll
     for (int c = 0; c < R; ++c) corr += (TA)d[c] * ((TA)b[(size_t)row * R + c] - rowsum[c]);
@@ -419,39 +442,40 @@ __global__ void __launch_bounds__(128) galerkin_ap_block_kernel(int ap_nb, const
     for (int c = 0; c < NS; ++c) out[r * NS + c] = acc[r][c];
 }
 
+// AP[r] = sum over the plan of A_k P_q   (B x B times B x 7)
 template <typename T, int B>
-__global__ void __launch_bounds__(128) galerkin_ac_block_kernel(int ac_nb, const int32_t* __restrict__ ac_ptr,
-                                                                const int32_t* __restrict__ pairs,
-                                                                const T* __restrict__ p_v, const T* __restrict__ ap_v,
-                                                                T* __restrict__ c_v) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= ac_nb) return;
-  T acc[NS][NS];
+__global__ void galerkin_ap_kernel(int ap_nb, const int32_t* __restrict__ ap_ptr, const int32_t* __restrict__ pairs,
+                                   const T* __restrict__ a_v, const T* __restrict__ p_v, T* __restrict__ ap_v) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = (int)(t / (B * NS)), e = (int)(t % (B * NS));
+  if (o >= ap_nb) return;
+  const int r = e / NS, c = e % NS;
+  T acc = 0;
+  for (int s = ap_ptr[o]; s < ap_ptr[o + 1]; ++s) {
+    const T* a = a_v + (size_t)pairs[2 * s] * (B * B) + r * B;
+    const T* p = p_v + (size_t)pairs[2 * s + 1] * (B * NS) + c;
 #pragma unroll
-  for (int r = 0; r < NS; ++r)
-#pragma unroll
-    for (int c = 0; c < NS; ++c) acc[r][c] = 0;
-  for (int s = ac_ptr[o]; s < ac_ptr[o + 1]; ++s) {
-    const T* p = p_v + (size_t)pairs[2 * s] * (B * NS);
-    const T* ap = ap_v + (size_t)pairs[2 * s + 1] * (B * NS);
-#pragma unroll
-    for (int m = 0; m < B; ++m) {
-      T apm[NS];
-#pragma unroll
-      for (int c = 0; c < NS; ++c) apm[c] = ap[m * NS + c];
-#pragma unroll
-      for (int r = 0; r < NS; ++r) {
-        const T pr = p[m * NS + r];
-#pragma unroll
-        for (int c = 0; c < NS; ++c) acc[r][c] += pr * apm[c];
-      }
-    }
+    for (int m = 0; m < B; ++m) acc += a[m] * p[m * NS];
   }
-  T* out = c_v + (size_t)o * (NS * NS);
+  ap_v[(size_t)o * (B * NS) + e] = acc;
+}
+
+// Ac[o] = sum over the plan of P_q^T AP_r   (7 x B times B x 7)
+template <typename T, int B>
+__global__ void galerkin_ac_kernel(int ac_nb, const int32_t* __restrict__ ac_ptr, const int32_t* __restrict__ pairs,
+                                   const T* __restrict__ p_v, const T* __restrict__ ap_v, T* __restrict__ c_v) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = (int)(t / (NS * NS)), e = (int)(t % (NS * NS));
+  if (o >= ac_nb) return;
+  const int r = e / NS, c = e % NS;
+  T acc = 0;
+  for (int s = ac_ptr[o]; s < ac_ptr[o + 1]; ++s) {
+    const T* p = p_v + (size_t)pairs[2 * s] * (B * NS) + r;
+    const T* ap = ap_v + (size_t)pairs[2 * s + 1] * (B * NS) + c;
 #pragma unroll
-  for (int r = 0; r < NS; ++r)
-#pragma unroll
-    for (int c = 0; c < NS; ++c) out[r * NS + c] = acc[r][c];
+    for (int m = 0; m < B; ++m) acc += p[m * NS] * ap[m * NS];
+  }
+  c_v[(size_t)o * (NS * NS) + e] = acc;
 }
 
 template <typename T>
@@ -685,17 +709,17 @@ inline int grid_stride_blocks(long n) {
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-template <typename TV, typename TX, typename TA, int R, int C, int MODE>
+template <typename TV, typename TX, typename TA, int R, int C, int MODE, typename TD = TV>
 static void bsr_launch(int n, const int32_t* rp, const int32_t* ci, const void* vals, const TX* x, const TX* b,
                        const void* dinv, TA omega, TX* y, cudaStream_t s, int cls) {
   if constexpr (R == 7) {
     if (n == 0) return;
     if (n < 4096)
-      FSI_LAUNCH(cls, s, bsr7_cta_kernel<TV, TX, TA, C, MODE><<<n, 224, 0, s>>>(
-          n, rp, ci, (const TV*)vals, x, b, (const TV*)dinv, omega, y));
+      FSI_LAUNCH(cls, s, bsr7_cta_kernel<TV, TX, TA, C, MODE, TD><<<n, 224, 0, s>>>(
+          n, rp, ci, (const TV*)vals, x, b, (const TD*)dinv, omega, y));
     else
-      FSI_LAUNCH(cls, s, bsr7_kernel<TV, TX, TA, C, MODE><<<blocks_for((long)n * 32, 128), 128, 0, s>>>(
-          n, rp, ci, (const TV*)vals, x, b, (const TV*)dinv, omega, y));
+      FSI_LAUNCH(cls, s, bsr7_kernel<TV, TX, TA, C, MODE, TD><<<blocks_for((long)n * 32, 128), 128, 0, s>>>(
+          n, rp, ci, (const TV*)vals, x, b, (const TD*)dinv, omega, y));
     return;
   }
   constexpr int LN = Lanes<R>::v;
@@ -850,9 +874,18 @@ static void galerkin_t(Level& L, Level& C, bool filter, cudaStream_t s) {
                                                               dsm, (const T*)L.ptent, (const T*)L.w_v,
                                                               (T)L.omega_p, (T*)L.p_v));
   FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_pt_kernel<T, B><<<blocks_for(pe, 256), 256, 0, s>>>(L.p_nb, L.pt_src, (const T*)L.p_v, (T*)L.pt_v));
-  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_block_kernel<T, B><<<blocks_for(L.ap_nb, 128), 128, 0, s>>>(
-      L.ap_nb, L.ap_ptr, L.ap_pairs, (const T*)L.vals, (const T*)L.p_v, (T*)L.ap_v));
-  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ac_block_kernel<T, B><<<blocks_for(C.nb, 128), 128, 0, s>>>(
+  // A P: one thread per output block on the 4x4 level (16 x 28 register
+  // tile, each A block read once per output block), one thread per output
+  // entry on the 7x7 levels (per-entry threads of one output block share its
+  // pair blocks through L1).  P^T (A P): one thread
+  // per entry everywhere.  Both choices measured faster on the 393k-tet tube.
+  if constexpr (B == 4)
+    FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_block_kernel<T, B><<<blocks_for(L.ap_nb, 128), 128, 0, s>>>(
+        L.ap_nb, L.ap_ptr, L.ap_pairs, (const T*)L.vals, (const T*)L.p_v, (T*)L.ap_v));
+  else
+    FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_kernel<T, B><<<blocks_for((long)L.ap_nb * B * NS, 256), 256, 0, s>>>(
+        L.ap_nb, L.ap_ptr, L.ap_pairs, (const T*)L.vals, (const T*)L.p_v, (T*)L.ap_v));
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ac_kernel<T, B><<<blocks_for((long)C.nb * NS * NS, 256), 256, 0, s>>>(
       C.nb, L.ac_ptr, L.ac_pairs, (const T*)L.p_v, (const T*)L.ap_v, (T*)C.vals));
   if (L.n_fix > 0)
     FSI_LAUNCH(fsi::KC_GALERKIN, s, identity_fix_kernel<T><<<blocks_for(L.n_fix, 128), 128, 0, s>>>(L.n_fix, L.fix_blk, L.fix_dof, (T*)C.vals));
@@ -864,6 +897,18 @@ void launch_galerkin(Level& L, Level& C, bool fp32, bool filter, cudaStream_t s)
   } else {
     if (L.bs == 4) galerkin_t<double, 4>(L, C, filter, s); else galerkin_t<double, 7>(L, C, filter, s);
   }
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+__global__ void values_to_bf16_kernel(long m, const float* __restrict__ x, __nv_bfloat16* __restrict__ y) {
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (long)gridDim.x * blockDim.x)
+    y[q] = __float2bfloat16_rn(x[q]);
+}
+
+void launch_values_to_bf16(const Level& L, cudaStream_t s) {
+  const long m = (long)L.nb * L.bs * L.bs;
+  FSI_LAUNCH(fsi::KC_GALERKIN, s, values_to_bf16_kernel<<<grid_stride_blocks(m), 256, 0, s>>>(
+      m, (const float*)L.vals, (__nv_bfloat16*)L.vals_lp));
   FSI_CUDA_TRY(cudaGetLastError());
 }
 
@@ -895,6 +940,14 @@ static void smooth_b(const Level& L, T omega, int sweeps, bool zero_start, cudaS
     }
   }
   for (; k < sweeps; ++k) {
+    if constexpr (B == 7 && std::is_same<T, float>::value) {
+      if (L.vals_lp) {
+        bsr_launch<__nv_bfloat16, float, float, 7, 7, 2, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp, x, b, L.dinv,
+                                                                 omega, x2, s, fsi::KC_COARSE_BSR);
+        std::swap(x, x2);
+        continue;
+      }
+    }
     bsr_launch<T, T, T, B, B, 2>(L.n, L.row_ptr, L.col_idx, L.vals, x, b, L.dinv, omega, x2, s, (B == 4 ? fsi::KC_JACOBI0 : fsi::KC_COARSE_BSR));
     std::swap(x, x2);
   }
@@ -936,8 +989,18 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
                                  (T*)L.r, s, fsi::KC_BSR0);
     bsr_launch<T, T, T, 7, 4, 0>(Lc.n, L.pt_rp, L.pt_ci, L.pt_v, (const T*)L.r, nullptr, nullptr, T(0), (T*)Lc.b, s, fsi::KC_TRANSFER);
   } else {
-    bsr_launch<T, T, T, 7, 7, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
-                                 (T*)L.r, s, fsi::KC_COARSE_BSR);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (L.vals_lp) {
+        bsr_launch<__nv_bfloat16, float, float, 7, 7, 1, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp,
+                                                                 (const float*)L.x, (const float*)L.b, nullptr,
+                                                                 0.0f, (float*)L.r, s, fsi::KC_COARSE_BSR);
+        done = true;
+      }
+    }
+    if (!done)
+      bsr_launch<T, T, T, 7, 7, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
+                                   (T*)L.r, s, fsi::KC_COARSE_BSR);
     bsr_launch<T, T, T, 7, 7, 0>(Lc.n, L.pt_rp, L.pt_ci, L.pt_v, (const T*)L.r, nullptr, nullptr, T(0), (T*)Lc.b, s, fsi::KC_TRANSFER);
   }
   vcycle<T>(h, level + 1, s);

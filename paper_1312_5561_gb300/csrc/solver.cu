@@ -200,6 +200,10 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
     upload_pattern(C, s);
     C.vals = upload_values(A.v, f32, s);
     C.dinv = upload_values(hl[l].Dinv, f32, s);
+    if (f32 && h.opts.coarse_bf16 && l + 1 < nl) {   // the coarsest level is solved, not smoothed
+      C.vals_lp = dalloc<char>(2 * (size_t)C.nb * C.bs * C.bs);
+      launch_values_to_bf16(C, s);
+    }
     alloc_level_vectors(C, f32);
     h.levels.push_back(std::move(C));
   }
@@ -268,6 +272,7 @@ void amg_numeric(Handle& h, cudaStream_t s) {
   for (int l = 0; l + 1 < nl; ++l) {
     if (l > 0) launch_block_inverse(h.levels[l], f32, h.d_err, s);
     launch_galerkin(h.levels[l], h.levels[l + 1], f32, h.filter_p, s);
+    if (h.levels[l + 1].vals_lp) launch_values_to_bf16(h.levels[l + 1], s);
   }
   launch_coarse_factor(h, f32, s);
 }
@@ -386,32 +391,22 @@ int fgmres(Handle& h, const double* b, double* x, double rtol, int maxit, double
       double* w = V + (size_t)(j + 1) * n;
       precondition(h, vj, zj, s);
       apply_operator(h, zj, w, s);
-      // pass 1: h = V^T w and ||w||^2 in one reduction (w is vector j+1)
+      // pass 1: h1 = V^T w (w is vector j+1); the update reads h1 from device
+      // memory, so the host waits only once, after pass 2
       dots(h, V, n, j + 2, w, n, h.d_dots, s);
-      FSI_CUDA_TRY(cudaMemcpyAsync(h.h_dots, h.d_dots, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
-      FSI_CUDA_TRY(cudaStreamSynchronize(s));
-      const double w2 = h.h_dots[j + 1];
-      double proj = 0.0;
-      for (int i = 0; i <= j; ++i) {
-        H[(size_t)i * m + j] = h.h_dots[i];
-        proj += h.h_dots[i] * h.h_dots[i];
-      }
       multi_axpy(h.d_dots, V, j + 1, n, w, -1.0, s);
-      double hn2 = w2 - proj;
-      {
-        // pass 2
-        dots(h, V, n, j + 2, w, n, h.d_dots + kDotH2, s);
-        FSI_CUDA_TRY(cudaMemcpyAsync(h.h_dots + kDotH2, h.d_dots + kDotH2, sizeof(double) * (j + 2),
-                                     cudaMemcpyDeviceToHost, s));
-        FSI_CUDA_TRY(cudaStreamSynchronize(s));
-        double proj2 = 0.0;
-        for (int i = 0; i <= j; ++i) {
-          H[(size_t)i * m + j] += h.h_dots[kDotH2 + i];
-          proj2 += h.h_dots[kDotH2 + i] * h.h_dots[kDotH2 + i];
-        }
-        multi_axpy(h.d_dots + kDotH2, V, j + 1, n, w, -1.0, s);
-        hn2 = h.h_dots[kDotH2 + j + 1] - proj2;
+      // pass 2: h2 = V^T w and ||w||^2 of the once-orthogonalised w
+      dots(h, V, n, j + 2, w, n, h.d_dots + kDotH2, s);
+      FSI_CUDA_TRY(cudaMemcpyAsync(h.h_dots, h.d_dots, sizeof(double) * (kDotH2 + j + 2), cudaMemcpyDeviceToHost,
+                                   s));
+      FSI_CUDA_TRY(cudaStreamSynchronize(s));
+      double proj2 = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        H[(size_t)i * m + j] = h.h_dots[i] + h.h_dots[kDotH2 + i];
+        proj2 += h.h_dots[kDotH2 + i] * h.h_dots[kDotH2 + i];
       }
+      multi_axpy(h.d_dots + kDotH2, V, j + 1, n, w, -1.0, s);
+      const double hn2 = h.h_dots[kDotH2 + j + 1] - proj2;
       const double hn = std::sqrt(std::max(hn2, 0.0));
       H[(size_t)(j + 1) * m + j] = hn;
       if (hn > 0.0) scale_copy(1.0 / hn, w, w, n, s);
@@ -792,6 +787,7 @@ static void destroy_impl(Handle* hp) {
   if (h.stream) cudaStreamSynchronize(h.stream);
   for (size_t l = 0; l < h.levels.size(); ++l) {
     Level& L = h.levels[l];
+    dfree(L.vals_lp);
     for (void* p : {(void*)L.row_ptr, (void*)L.col_idx, (void*)L.diag_idx, (void*)L.block_row, L.vals, L.dinv,
                     (void*)L.p_rp, (void*)L.p_ci, L.p_v, (void*)L.pt_rp, (void*)L.pt_ci, L.pt_v, L.x, L.x2, L.b,
                     L.r, (void*)L.agg, L.ptent, (void*)L.freem, (void*)L.p_brow, (void*)L.w_ptr, (void*)L.w_k,

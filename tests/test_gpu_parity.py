@@ -173,7 +173,9 @@ def small_artery():
     dict(krylov=1, precond=1, precision=1, krylov_rtol=1e-10, max_krylov=3000),
     # the paper's Vanka smoother (Sec. 4.5) on the finest level, FP32
     dict(smoother=1, precision=1, krylov_rtol=1e-12, max_krylov=1000),
-], ids=["fgmres_amg", "bicgstab_pl_fp32", "vanka_fp32"])
+    # FP32 + refinement with BF16 coarse-level operators in the V-cycle
+    dict(precision=1, coarse_bf16=1, krylov_rtol=1e-12, max_krylov=1000),
+], ids=["fgmres_amg", "bicgstab_pl_fp32", "vanka_fp32", "coarse_bf16"])
 def test_newton_small_artery_pressure_ramp(small_artery, solver_kw):
     """Two-layer artery, 64 x 8 x 8 hexes (length 0.5), internal pressure
     ramped to 0.64 in 4 steps (the same increments as 0 -> 1.6 in 10)."""
