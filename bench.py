@@ -120,6 +120,12 @@ def job_value(steps_per_s_max_time, world):
 
 
 # ------------------------------------------------------------------ GPU arm
+# DRAM bytes (read + write) per launch of the finest-level block-Jacobi sweep,
+# from the ncu full capture summarised in profiles/jacobi0_tube393k_full.md
+# (393k-tet tube, FP32 values).  Reset to None whenever that kernel changes.
+JACOBI0_TRAFFIC = {("tube", 128, "fp32"): 79_937_664}
+
+
 def jacobi0_bytes(n, nb, fp32):
     """Algorithmic bytes of one finest-level damped block-Jacobi sweep:
     4x4 values + column index per block, row pointer, x / b / y vectors and
@@ -250,13 +256,14 @@ def run_gpu(args, rank, world):
     peaks, src = _peaks()
     roof = None
     jt, jc = prof["jacobi0"]
-    if jc > 0:
+    if jc > 0 and args.smoother != "vanka":   # with Vanka this class holds the patch sweeps
         per_launch_s = jt * 1e-3 / jc
         byt = jacobi0_bytes(L0n, L0nb, prec == 1)
         ach = byt / per_launch_s / 1e9
         roof = {"kernel": "bsr_kernel<...,4,4,MODE=2> (finest-level block-Jacobi sweep)", "bound": "hbm",
                 "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(ach / peaks["hbm_gbs"], 3), "traffic": None, "peak_source": src,
+                "frac": round(ach / peaks["hbm_gbs"], 3),
+                "traffic": JACOBI0_TRAFFIC.get((args.config, args.nz, args.precision)), "peak_source": src,
                 "bytes_per_launch": int(byt), "avg_launch_us": round(per_launch_s * 1e6, 2),
                 "timing": f"CUDA events around each launch over a {args.prof_steps}-step kernel-timing pass "
                           f"following the timed region (same workload, V-cycle launched eagerly)"}

@@ -137,7 +137,29 @@ __global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const in
   TA acc = 0;
   if (row < n && lane < 4 * R) {
     const int k1 = row_ptr[row + 1];
-    for (int k = row_ptr[row] + j; k < k1; k += 4) {
+    int k = row_ptr[row] + j;
+    if constexpr (C == R) {
+      // two blocks per slot and step: both blocks' loads are issued before the products
+      for (; k + 4 < k1; k += 8) {
+        const TV* a0 = vals + (size_t)k * (R * C) + r * C;
+        const TV* a1 = vals + (size_t)(k + 4) * (R * C) + r * C;
+        const TX* x0 = x + (size_t)col_idx[k] * C;
+        const TX* x1 = x + (size_t)col_idx[k + 4] * C;
+        TA v0[C], v1[C], y0[C], y1[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          v0[c] = (TA)a0[c];
+          v1[c] = (TA)a1[c];
+          y0[c] = (TA)x0[c];
+          y1[c] = (TA)x1[c];
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc += v0[c] * y0[c];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc += v1[c] * y1[c];
+      }
+    }
+    for (; k < k1; k += 4) {
       const TV* a = vals + (size_t)k * (R * C) + r * C;
       const TX* xv = x + (size_t)col_idx[k] * C;
       if constexpr (C == 4) {
