@@ -181,6 +181,8 @@ def run_gpu(args, rank, world):
     kry = dict(krylov=1, precond=1, max_krylov=3000) if args.solver == "bicgstab-pl" else dict(max_krylov=600)
     if args.coarse_bf16:
         kry.update(coarse_bf16=1)
+    agg = args.aggregation or ("grow" if args.config == "refined" else "ring")
+    kry.update(aggregation=1 if agg == "grow" else 0)
     if args.smoother == "vanka":       # the paper's Vanka smoother on the finest level (Sec. 4.5)
         kry.update(smoother=1, vanka_omega=0.86, nu_pre=args.nu, nu_post=args.nu)
     solver = SolidSolver(mesh, precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=int(args.graphs),
@@ -345,6 +347,8 @@ def main():
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "vanka"])
     ap.add_argument("--nu", type=int, default=1, help="Vanka sweeps before / after the coarse correction")
     ap.add_argument("--coarse-bf16", type=int, default=0, help="BF16 coarse-level operators in the V-cycle")
+    ap.add_argument("--aggregation", default=None, choices=["ring", "grow"],
+                    help="AMG aggregation (default: grow for the 16-layer refined tube, ring otherwise)")
     ap.add_argument("--compare-paper-solver", action="store_true",
                     help="also time BiCGStab + P_L (the paper's solid solver) on the same workload")
     args = ap.parse_args()
@@ -410,6 +414,7 @@ def main():
                        finest_smoother=(f"Vanka, {args.nu}+{args.nu} sweeps, omega 0.86" if args.smoother == "vanka"
                                         else "damped block Jacobi, 4+4 sweeps, omega 0.7"),
                        coarse_operators="BF16 (V-cycle reads)" if args.coarse_bf16 else "FP32",
+                       aggregation=(args.aggregation or ("grow" if args.config == "refined" else "ring")),
                        krylov_its_per_step=round(res["krylov_per_step"], 1),
                        krylov_cap_hits_in_timed_steps=res["krylov_cap_hits"], amg_levels=res["levels"]),
         "element_tangents_per_s": res["tangents_per_s"] * world,

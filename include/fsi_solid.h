@@ -105,6 +105,16 @@ enum { FSI_SMOOTHER_JACOBI = 0, FSI_SMOOTHER_VANKA = 1 };
  *                        Eq. lpreschur (M_p the P1 pressure mass matrix, kappa
  *                        per element).  The paper pairs it with BiCGStab. */
 enum { FSI_PRECOND_AMG = 0, FSI_PRECOND_BLOCK_LT = 1 };
+/* Aggregation of the smoothed-aggregation hierarchy (set-up, host, once).
+ *  FSI_AGG_RING  a root node takes its 7 strongest free neighbours (block
+ *                Frobenius norm), leftovers join their strongest neighbour's
+ *                aggregate (default).
+ *  FSI_AGG_GROW  an aggregate grows one node at a time by the strongest
+ *                connection from any member, up to 8 nodes: on walls meshed
+ *                with many thin element layers it forms lines across the wall,
+ *                where FSI_AGG_RING coarsens along the weak directions and the
+ *                Krylov iteration stalls. */
+enum { FSI_AGG_RING = 0, FSI_AGG_GROW = 1 };
 
 /* Solver options.  Defaults come from fsi_solid_default_opts(). */
 typedef struct {
@@ -137,6 +147,7 @@ typedef struct {
                                <= 0: c10 of material 0 */
   double vanka_omega;       /* relaxation of the Vanka update (the paper: 0.78 for
                                Mooney-Rivlin, 0.86 for the artery) */
+  int32_t aggregation;      /* FSI_AGG_* */
   int32_t coarse_bf16;      /* FSI_PREC_FP32_IR only: the V-cycle reads the coarse-level
                                (7x7) operators as BF16 copies (smoothing and residual;
                                FP32 accumulation); the Galerkin products, transfers,

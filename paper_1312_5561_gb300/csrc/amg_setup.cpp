@@ -84,7 +84,12 @@ inline void gemm_tn_acc(const double* A, const double* B, double* Y, int bk, int
 //     neighbour (decided against the state after step 1);
 //  3. the rest become singletons.
 // Aggregates are renumbered component-major (stable).
-int aggregate_capped(const HostBsr& A, const std::vector<int32_t>& comp, int cap, std::vector<int32_t>& agg) {
+// grow = false: a root takes its cap-1 strongest free neighbours (1-ring);
+// grow = true:  the aggregate grows one node at a time by the strongest
+//               connection from any member to a free node, so that on thin,
+//               stretched elements it becomes a line across the wall.
+int aggregate_capped(const HostBsr& A, const std::vector<int32_t>& comp, int cap, bool grow,
+                     std::vector<int32_t>& agg) {
   const int n = A.n;
   const int bb = A.br * A.bc;
   std::vector<double> w(A.nb());
@@ -96,6 +101,7 @@ int aggregate_capped(const HostBsr& A, const std::vector<int32_t>& comp, int cap
   agg.assign(n, -1);
   int na = 0;
   std::vector<std::pair<double, int>> cand;
+  std::vector<int> members;
   for (int i = 0; i < n; ++i) {
     if (agg[i] >= 0) continue;
     cand.clear();
@@ -104,6 +110,26 @@ int aggregate_capped(const HostBsr& A, const std::vector<int32_t>& comp, int cap
       if (j != i && agg[j] < 0) cand.push_back({-w[k], j});
     }
     if (cand.empty()) continue;
+    if (grow) {
+      // grow by the strongest connection from any member to a free node
+      agg[i] = na;
+      members.assign(1, i);
+      while ((int)members.size() < cap) {
+        double best = -1.0;
+        int bj = -1;
+        for (int m : members)
+          for (int k = A.rp[m]; k < A.rp[m + 1]; ++k) {
+            const int j = A.ci[k];
+            if (j == m || agg[j] >= 0) continue;
+            if (w[k] > best || (w[k] == best && j < bj)) { best = w[k]; bj = j; }
+          }
+        if (bj < 0) break;
+        agg[bj] = na;
+        members.push_back(bj);
+      }
+      ++na;
+      continue;
+    }
     std::sort(cand.begin(), cand.end());
     agg[i] = na;
     for (int q = 0; q < (int)cand.size() && q < cap - 1; ++q) agg[cand[q].second] = na;
@@ -268,7 +294,7 @@ void block_inverses(const HostBsr& A, std::vector<double>& Dinv) {
 
 void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
                         const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap, bool filter,
-                        std::vector<HostLevel>& levels, HostCoarse& coarse) {
+                        std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow) {
   levels.clear();
   levels.emplace_back();
   levels[0].A = A0;
@@ -310,7 +336,7 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
     }
     if (max_run <= coarse_max || l + 1 >= max_levels) break;
     std::vector<int32_t> agg;
-    const int nc = aggregate_capped(A, L.comp, cap, agg);
+    const int nc = aggregate_capped(A, L.comp, cap, grow, agg);
     if (nc >= n) break;
     // tentative prolongator (one b x 7 block per fine node) and coarse null space
     std::vector<std::vector<int32_t>> members(nc);

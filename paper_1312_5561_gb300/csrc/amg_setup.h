@@ -47,8 +47,9 @@ struct HostCoarse {
 // filter: smooth the prolongator with A minus its displacement-pressure
 // couplings (needed when inertia dominates the displacement block: the PSPG
 // inertia coupling then blows up the pressure rows of D^-1 A).
+// grow: aggregates grow along the strongest connections (see aggregate_capped).
 void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
                         const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap, bool filter,
-                        std::vector<HostLevel>& levels, HostCoarse& coarse);
+                        std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow = false);
 
 }  // namespace fsi

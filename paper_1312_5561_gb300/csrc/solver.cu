@@ -188,7 +188,7 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
   HostCoarse hc;
   h.filter_p = h.opts.inertia_coef > 0.0;
   build_sa_hierarchy(A0, free0, X, comp0, std::max(1, h.opts.coarse_max_nodes), std::max(1, h.opts.max_levels),
-                     8, h.filter_p, hl, hc);
+                     8, h.filter_p, hl, hc, h.opts.aggregation == FSI_AGG_GROW);
   const int nl = (int)hl.size();
   const size_t ts = f32 ? 4 : 8;
   for (int l = 1; l < nl; ++l) {
@@ -565,6 +565,8 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
     throw ArgError("unknown preconditioner");
   if (h.opts.smoother != FSI_SMOOTHER_JACOBI && h.opts.smoother != FSI_SMOOTHER_VANKA)
     throw ArgError("unknown smoother");
+  if (h.opts.aggregation != FSI_AGG_RING && h.opts.aggregation != FSI_AGG_GROW)
+    throw ArgError("unknown aggregation");
   h.opts.restart = std::min(std::max(h.opts.restart, 1), kMaxRestart);
   if (h.opts.krylov == FSI_KRYLOV_BICGSTAB) h.opts.restart = std::max(h.opts.restart, 2);   // BiCGStab work vectors
   h.m = h.opts.restart;

@@ -315,3 +315,19 @@ def test_vanka_solve_is_bitwise_reproducible(precision):
     x2, i2 = solver.linear_solve(_t(b))
     assert i1.krylov_its_last == i2.krylov_its_last
     assert torch.equal(x1, x2)
+
+
+def test_grown_aggregates_on_a_wall_of_sixteen_thin_layers():
+    """Tube wall meshed with 16 element layers (the refined tube's radial
+    resolution), pressure ramp to 0.32 in 2 steps: with aggregates grown along
+    the strongest connections the solve converges to the oracle's solution."""
+    from paper_1312_5561_gb300.binding import Load
+    mesh = artery_tube(n_theta=32, n_media=8, n_adv=8, n_z=4, length=0.25, materials=artery_layers(1.0e3))
+    solver = _solver(mesh, aggregation=1, precision=1, newton_rtol=1e-10, krylov_rtol=1e-12, max_krylov=1000)
+    state = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
+    for k in (1, 2):
+        info = solver.solve(state, Load(pressure=0.16 * k))
+        assert info.newton_its <= 8
+    ref = _oracle_ramp(mesh, 2, pressure=0.32)
+    got = state.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
