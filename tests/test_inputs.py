@@ -1,0 +1,55 @@
+"""The seeded input recipes and the benchmark's byte model (host logic, no GPU)."""
+import math
+import os
+import sys
+
+import numpy as np
+
+from fixtures import artery_layers, artery_tube, batched_tubes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _volumes(mesh):
+    X, T = mesh.X, mesh.tets
+    d = X[T[:, 1:]] - X[T[:, :1]]
+    return np.linalg.det(d) / 6.0
+
+
+def test_tube_sizes_and_orientation():
+    """64 x 8 x 128 hexahedra x 6 tets: 393,216 tets, 74,304 nodes (theta
+    periodic), all positively oriented, wall volume equal to the annulus."""
+    mesh = artery_tube(materials=artery_layers(1.0e3))
+    assert mesh.n_elems == 393216 and mesh.n_nodes == 64 * 9 * 129
+    v = _volumes(mesh)
+    assert (v > 0).all()
+    # polygonal annulus of 64 sides between r = 1 and r = 1.23, length 8
+    poly = 0.5 * 64 * math.sin(2 * math.pi / 64)
+    assert abs(v.sum() - poly * (1.23 ** 2 - 1.0) * 8.0) <= 1e-9 * v.sum()
+
+
+def test_batched_segments_recipe():
+    """Segments of the seed-4 recipe (the first 32 of the 256: the draws are
+    sequential per segment): contiguous node and element ranges, sizes drawn
+    in [5e3, 2e5] up to the rounding of n_z, pressure in [0.5, 2.0]."""
+    mesh = batched_tubes(32, seed=4)
+    seg = mesh.seg_node
+    assert (np.diff(seg) >= 0).all() and seg[0] == 0 and seg[-1] == 31
+    sege = mesh.seg_elem
+    assert (np.diff(sege) >= 0).all()
+    counts = np.bincount(sege, minlength=32)
+    # n_z = max(2, round(n_e / (6 n_r n_theta))) moves a segment by at most half a ring of hexahedra
+    assert counts.min() >= 5.0e3 - 3 * 8 * 64 and counts.max() <= 2.0e5 + 3 * 8 * 64
+    assert (mesh.face_pressure >= 0.5).all() and (mesh.face_pressure <= 2.0).all()
+    assert (_volumes(mesh) > 0).all()
+    # every tet lies in one segment
+    assert (seg[mesh.tets] == sege[:, None]).all()
+
+
+def test_bench_byte_model_of_the_block_jacobi_sweep():
+    """The roofline numerator: n_b (64 + 4) + 4 (n + 1) + n (48 + 64) bytes per
+    FP32 sweep, 79,622,148 at the 393k-tet tube (1,044,160 blocks)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.jacobi0_bytes(74304, 1044160, True) == 1044160 * 68 + 4 * 74305 + 74304 * 112 == 79622148
+    assert bench.jacobi0_bytes(74304, 1044160, False) == 1044160 * 132 + 4 * 74305 + 74304 * 224
