@@ -177,13 +177,13 @@ def run_gpu(args, rank, world):
     prec = 1 if args.precision == "fp32" else 0
     t_create = time.perf_counter()
     # fgmres-amg: FGMRES(100) + one AMG V-cycle on the whole u-p tangent;
-    # bicgstab-pl: the paper's solid solver, BiCGStab + block-triangular P_L (Sec. 4.4.2)
+    # bicgstab-pl: the paper's solid solver, BiCGStab + block-triangular P_L (Sec. 5.4.2)
     kry = dict(krylov=1, precond=1, max_krylov=3000) if args.solver == "bicgstab-pl" else dict(max_krylov=600)
     if args.coarse_bf16:
         kry.update(coarse_bf16=1)
     agg = args.aggregation or ("grow" if args.config == "refined" else "ring")
     kry.update(aggregation=1 if agg == "grow" else 0)
-    if args.smoother == "vanka":       # the paper's Vanka smoother on the finest level (Sec. 4.5)
+    if args.smoother == "vanka":       # the paper's Vanka smoother on the finest level (Sec. 5.5.2)
         kry.update(smoother=1, vanka_omega=0.86, nu_pre=args.nu, nu_post=args.nu)
     solver = SolidSolver(mesh, precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=int(args.graphs),
                          amg_lag=int(args.amg_lag), **kry)
@@ -434,7 +434,7 @@ def main():
                              "speedup_vs_plain_fp64": res["steps_per_s"] / other["steps_per_s"],
                              "roofline": other["roofline"], "dominant_kernel_class": other["dominant"]}
     if paper is not None:
-        out["paper_solver"] = {"solver": "BiCGStab + block-triangular P_L (Sec. 4.4.2), same precision",
+        out["paper_solver"] = {"solver": "BiCGStab + block-triangular P_L (Sec. 5.4.2), same precision",
                                "value": paper["steps_per_s"] * world, "ms_per_step": paper["ms_per_step"],
                                "krylov_its_per_step": round(paper["krylov_per_step"], 1),
                                "krylov_cap_hits_in_timed_steps": paper["krylov_cap_hits"],

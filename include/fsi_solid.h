@@ -84,7 +84,7 @@ enum { FSI_KRYLOV_FGMRES = 0, FSI_KRYLOV_BICGSTAB = 1 };
 /* Smoother of the finest AMG level (coarser levels always use damped block
  * Jacobi).
  *  FSI_SMOOTHER_JACOBI  damped 4x4 block Jacobi, damping omega.
- *  FSI_SMOOTHER_VANKA   the multiplicative Vanka smoother of Sec. 4.5
+ *  FSI_SMOOTHER_VANKA   the multiplicative Vanka smoother of Sec. 5.5.2
  *                       (Eq. locsys, vankasmooth): one patch per pressure
  *                       unknown p_i holding p_i and the displacements of the
  *                       nodes that B2 couples to it (node i and its mesh
@@ -97,7 +97,7 @@ enum { FSI_KRYLOV_FGMRES = 0, FSI_KRYLOV_BICGSTAB = 1 };
 enum { FSI_SMOOTHER_JACOBI = 0, FSI_SMOOTHER_VANKA = 1 };
 /* Preconditioner of the Krylov method.
  *  FSI_PRECOND_AMG       one AMG V-cycle on the whole u-p tangent K (default).
- *  FSI_PRECOND_BLOCK_LT  the block lower-triangular P_L of Sec. 4.4.2,
+ *  FSI_PRECOND_BLOCK_LT  the block lower-triangular P_L of Sec. 5.4.2,
  *                        Eq. lpre: x_u = A~^-1 r_u by one AMG V-cycle on the
  *                        displacement block A, then
  *                        x_p = S~^-1 (B2 x_u - r_p) with the Schur-complement

@@ -796,7 +796,7 @@ void launch_residual_f64(const Level& L, const void* vals, const double* b, cons
   FSI_CUDA_TRY(cudaGetLastError());
 }
 
-// ---- block lower-triangular preconditioner P_L (Sec. 4.4.2, Eq. lpre)
+// ---- block lower-triangular preconditioner P_L (Sec. 5.4.2, Eq. lpre)
 // A from K: one thread per block entry.  Entries coupling u and p are dropped;
 // the pressure row of a diagonal block becomes (0 0 0 1), of any other block 0.
 template <typename T>

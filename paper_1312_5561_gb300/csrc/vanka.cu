@@ -1,4 +1,4 @@
-// Multiplicative Vanka smoother of the finest AMG level (Sec. 4.5, Eq. locsys
+// Multiplicative Vanka smoother of the finest AMG level (Sec. 5.5.2, Eq. locsys
 // and vankasmooth).
 //
 // Patch P_i: the pressure unknown p_i and the displacement unknowns of every

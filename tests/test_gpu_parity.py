@@ -169,9 +169,9 @@ def small_artery():
 
 @pytest.mark.parametrize("solver_kw", [
     dict(krylov_rtol=1e-12, max_krylov=1000),
-    # the paper's solid solver: BiCGStab with P_L (Sec. 4.4.2), FP32 tangent and V-cycle
+    # the paper's solid solver: BiCGStab with P_L (Sec. 5.4.2), FP32 tangent and V-cycle
     dict(krylov=1, precond=1, precision=1, krylov_rtol=1e-10, max_krylov=3000),
-    # the paper's Vanka smoother (Sec. 4.5) on the finest level, FP32
+    # the paper's Vanka smoother (Sec. 5.5.2) on the finest level, FP32
     dict(smoother=1, precision=1, krylov_rtol=1e-12, max_krylov=1000),
     # FP32 + refinement with BF16 coarse-level operators in the V-cycle
     dict(precision=1, coarse_bf16=1, krylov_rtol=1e-12, max_krylov=1000),
