@@ -66,15 +66,6 @@ void element_pattern(int n_nodes, int n_elems, const int32_t* tets, HostPattern&
 // Find block (i, j) in a pattern; -1 if absent.
 int32_t find_block(const HostPattern& pat, int32_t i, int32_t j);
 
-// Deterministic greedy aggregation of a node graph (see the definition in setup.cpp).
-// comp[i] = connected component (segment) of node i; aggregates never cross
-// components and are numbered component-major.  Returns the number of aggregates.
-int aggregate_nodes(const HostPattern& pat, const std::vector<int32_t>& comp, std::vector<int32_t>& agg);
-
-// Pattern of the Galerkin product P^T K P for a block-identity P over aggregates.
-void coarse_pattern(const HostPattern& fine, const std::vector<int32_t>& agg, int n_coarse,
-                    HostPattern& coarse);
-
 // ------------------------------------------------------------------ device level
 // One level of the AMG hierarchy.  Level 0 holds the assembled tangent (4x4
 // blocks); coarser levels hold Galerkin operators with 7x7 blocks.  P maps
