@@ -7,13 +7,16 @@
 // the relative residual ||R(v_k)|| <= eps_2 ||R(v_0)||; with adaptive_tol the
 // inner reduction follows eps_(1,k) = eps_(2,k-1)^2 (Sec. 4.4, end).
 //
-// The Krylov method is FGMRES(m) with classical Gram-Schmidt applied twice,
-// right-preconditioned by one V-cycle of an aggregation AMG on the 4x4 block
-// system (damped block-Jacobi smoothing, Galerkin coarse operators, a dense
-// block-diagonal solve on the coarsest level).  Vectors, orthogonalisation
-// and the outer residual are FP64; in FSI_PREC_FP32_IR the tangent and the
-// V-cycle are FP32 while the Newton residual stays FP64, so each Newton step
-// acts as one step of iterative refinement.
+// The Krylov method is FGMRES(m) with classical Gram-Schmidt applied twice
+// (or BiCGStab), right-preconditioned by one V-cycle of a smoothed-aggregation
+// AMG on the 4x4 block system (damped block-Jacobi or Vanka smoothing,
+// Galerkin coarse operators, a dense block-diagonal solve on the coarsest
+// level), or by the block-triangular P_L of Sec. 5.4.2.  Vectors,
+// orthogonalisation and the outer residual are FP64; in FSI_PREC_FP32_IR the
+// tangent and the V-cycle are FP32 while the Newton residual stays FP64, so
+// each Newton step acts as one step of iterative refinement.  The
+// Dirichlet-Neumann coupling loop of Sec. 5.1-5.2 (dn_impl) runs Newton solves
+// under a surrogate fluid load.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
