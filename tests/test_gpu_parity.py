@@ -331,3 +331,42 @@ def test_grown_aggregates_on_a_wall_of_sixteen_thin_layers():
     ref = _oracle_ramp(mesh, 2, pressure=0.32)
     got = state.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_newmark_advance_matches_the_oracle():
+    """fsi_solid_newmark_advance against the oracle's Newmark-beta bookkeeping
+    (Sec. 4.1.2): new acceleration, velocity and history, and d_(n) stored."""
+    from oracle import newmark as N
+    mesh = MESHES["cube_mr"]()
+    solver = _solver(mesh)
+    rng = np.random.default_rng(7)
+    n = mesh.n_nodes
+    state = rng.standard_normal((n, 4))
+    disp, vel, acc = (rng.standard_normal((n, 3)) for _ in range(3))
+    beta, gamma, dt = 0.625, 1.0, 0.01
+    a_ref, v_ref, h_ref = N.newmark_update(state[:, :3], disp, vel, acc, beta, gamma, dt)
+    D, Vv, A = _t(disp), _t(vel), _t(acc)
+    H = torch.zeros((n, 3), device="cuda", dtype=torch.float64)
+    solver.newmark_advance(_t(state), D, Vv, A, H, beta, gamma, dt)
+    assert np.array_equal(D.cpu().numpy(), state[:, :3])
+    for got, ref in ((A, a_ref), (Vv, v_ref), (H, h_ref)):
+        assert np.abs(got.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_inertia_residual_and_tangent_parity():
+    """Residual and tangent with the Newmark inertia terms (inertia coefficient
+    1 / (beta dt^2), rho = 1.2, a nodal history) against the oracle."""
+    from paper_1312_5561_gb300.binding import Load
+    mesh = artery_tube(n_theta=16, n_z=6, materials=artery_layers(1.0e3, rho=1.2))
+    c = 1.0 / (0.625 * 0.01 ** 2)
+    P = O.Problem(mesh, O.Options(inertia_coef=c))
+    s = _smooth_state(mesh, 4)
+    hist = c * s[:, :3] + np.random.default_rng(9).standard_normal((mesh.n_nodes, 3))
+    solver = _solver(mesh, inertia_coef=c)
+    R = solver.residual_tangent(_t(s), Load(pressure=1.3, hist=_t(hist))).cpu().numpy()
+    R_ref = P.residual(s, P.external_force(1.3), hist)
+    scale = np.abs(R_ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(R - R_ref) <= 1e-12 * np.maximum(scale, np.abs(R_ref).max() * 1e-3))
+    rp, ci, vals = solver.bsr()
+    Kg = _bsr_to_csr(rp, ci, vals, mesh.n_nodes)
+    assert _blockrow_rel_err(Kg, P.tangent(s, hist), mesh.n_nodes) <= 1e-12
