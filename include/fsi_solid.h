@@ -39,9 +39,7 @@ typedef enum {
   FSI_ERR_CUDA = -2,           /* a CUDA runtime call failed */
   FSI_ERR_OOM = -3,            /* device allocation failed */
   FSI_ERR_INVERTED = -4,       /* an element reached J <= 0 or a non-finite value */
-  FSI_ERR_NOT_CONVERGED = -5,  /* Newton or Krylov hit its iteration cap */
-  FSI_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
-  FSI_ERR_BOUNDS = -7          /* a bounds-checked gather/scatter index was invalid */
+  FSI_ERR_NOT_CONVERGED = -5   /* Newton or Krylov hit its iteration cap */
 } fsi_status;
 
 /* Material models (Sec. 2.3.1 and 2.3.2). */
@@ -182,6 +180,10 @@ typedef struct {
   double res;                /* ||R(v_k)||_2 at return */
   double inc_norm;           /* ||v_k - v_(k-1)||_2 of the last update */
   double lin_res;            /* relative residual of the last linear solve */
+  double inc_mnorm;          /* ||v_k - v_(k-1)||_M of the last update: the L2 norm of the
+                                displacement and pressure increment, sqrt(dv^T M dv) with
+                                M = diag[M_1, M_2] the P1 mass matrices, the quantity the
+                                paper's Newton stop (Sec. 4.4, Eq. newstop) measures */
 } fsi_info;
 
 /* Default options: FP64, FGMRES(100), block Jacobi 4+4 sweeps on the finest
@@ -367,16 +369,16 @@ fsi_status fsi_mlp_train_step(fsi_mlp_t h, const float* X, const float* T, int32
  * call cudaMalloc / cudaFree after start-up because those calls synchronise
  * the device and stall its other streams.  It needs no handle and allocates
  * nothing: its partial sums live in a fixed file-scope device array of
- * FSI_DOTS_STATIC_MAX_VECTORS x 256 doubles (64 KiB) that every GPU which
+ * FSI_DOTS_STATIC_MAX_VECTORS x 304 doubles (76 KiB) that every GPU which
  * loads the library keeps until the process exits.  k must lie in
  * [1, FSI_DOTS_STATIC_MAX_VECTORS] (FSI_ERR_ARG otherwise) and ldv >= n when
- * k > 1.  The sums use the same deterministic two-pass reduction as the
- * solver (one partial per CTA, then a fixed-order sum), so repeated calls
- * give identical results.  The first call on each device looks up the
- * array's device address on that device (make that first call before any
- * stream capture).  All calls share the one array: calls that overlap on the
- * GPU (different streams or threads) race and must be serialised by the
- * caller.  Returns after the work on `stream` has finished. */
+ * k > 1.  The sums use the solver's own deterministic two-pass reduction (304
+ * CTA partials, then a fixed-order sum), so repeated calls give identical
+ * results, bit-identical to the norms the solver reports.  Each call looks up
+ * the array's address in the current context of the current device.  All
+ * calls share the one array: calls that overlap on the GPU (different streams
+ * or threads) race and must be serialised by the caller.  Returns after the
+ * work on `stream` has finished. */
 #define FSI_DOTS_STATIC_MAX_VECTORS 32
 fsi_status fsi_dots_static(const double* V, int64_t ldv, int32_t k, const double* y, int64_t n, double* out,
                            void* stream);

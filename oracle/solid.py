@@ -333,6 +333,22 @@ class Problem:
             K = (Df @ K @ Df + sp.diags(1.0 - fr)).tocsr()
         return K
 
+    def mass_matrix(self):
+        """Consistent P1 mass matrix of one scalar field (CSR, n x n):
+        M_ab = int N_a N_b dV = V (1 + delta_ab) / 20 on each tetrahedron."""
+        tets = self.mesh.tets
+        Me = (self.V / 20.0)[:, None, None] * (np.ones((4, 4)) + np.eye(4))[None]
+        rows = np.repeat(tets, 4, axis=1).ravel()
+        cols = np.tile(tets, (1, 4)).ravel()
+        return sp.coo_matrix((Me.ravel(), (rows, cols)), shape=(self.n, self.n)).tocsr()
+
+    def mass_norm(self, dv):
+        """||dv||_M = sqrt(dv^T M dv), M = diag[M_1, M_2]: the L2 norm of the
+        displacement and pressure increment of Sec. 4.4 (Eq. newstop); M_1 is
+        the scalar mass matrix on each displacement component, M_2 on p."""
+        M = self.mass_matrix()
+        return float(np.sqrt(sum(dv[:, c] @ (M @ dv[:, c]) for c in range(4))))
+
     def apply_dirichlet(self, state, values):
         """Prescribed values go into the state at the start of a load step."""
         s = state.copy()

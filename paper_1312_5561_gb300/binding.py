@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 FSI_OK = 0
 STATUS = {0: "FSI_OK", -1: "FSI_ERR_ARG", -2: "FSI_ERR_CUDA", -3: "FSI_ERR_OOM", -4: "FSI_ERR_INVERTED",
-          -5: "FSI_ERR_NOT_CONVERGED", -6: "FSI_ERR_TIMEOUT", -7: "FSI_ERR_BOUNDS"}
+          -5: "FSI_ERR_NOT_CONVERGED"}
 
 # symbols declared in include/fsi_solid.h
 EXPORTS = [
@@ -69,7 +69,8 @@ class LoadDesc(C.Structure):
 class Info(C.Structure):
     _fields_ = [("newton_its", C.c_int32), ("krylov_its_total", C.c_int32), ("krylov_its_last", C.c_int32),
                 ("status", C.c_int32), ("guess_accepted", C.c_int32), ("n_levels", C.c_int32),
-                ("res0", C.c_double), ("res", C.c_double), ("inc_norm", C.c_double), ("lin_res", C.c_double)]
+                ("res0", C.c_double), ("res", C.c_double), ("inc_norm", C.c_double), ("lin_res", C.c_double),
+                ("inc_mnorm", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -579,6 +579,62 @@ __global__ void newmark_kernel(int n, const double* __restrict__ state, double* 
   hist[t] = dn / (beta * dt * dt) + v_new / (beta * dt) + (1.0 - 2.0 * beta) / (2.0 * beta) * a_new;
 }
 
+// ||x||_M^2 with M = diag[M_1, M_2], the P1 mass matrices of the displacement
+// components and of the pressure (Sec. 4.4, Eq. newstop): element e adds
+// sum_ab M_ab x_a . x_b = (V/20) (sum_a |x_a|^2 + |sum_a x_a|^2) over the
+// 4 unknowns per node (M_ab = V (1 + delta_ab) / 20).  Each CTA sums a fixed
+// grid-stride set of elements; a second pass adds the CTA partials in index
+// order, so the result is deterministic.
+constexpr int kNormThreads = 256;
+
+__device__ __forceinline__ double cta_sum(double v) {
+  __shared__ double w[kNormThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < kNormThreads / 32) ? w[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(kNormThreads) mass_norm_partial_kernel(int ne, const int32_t* __restrict__ conn,
+                                                                       const double* __restrict__ geo,
+                                                                       const double* __restrict__ x,
+                                                                       double* __restrict__ partial) {
+  double acc = 0.0;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (long)gridDim.x * blockDim.x) {
+    const int4 c = *reinterpret_cast<const int4*>(conn + 4 * e);
+    const int nd[4] = {c.x, c.y, c.z, c.w};
+    double sq = 0.0, sum[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const double2 lo = *reinterpret_cast<const double2*>(x + 4 * (size_t)nd[a]);
+      const double2 hi = *reinterpret_cast<const double2*>(x + 4 * (size_t)nd[a] + 2);
+      sq += lo.x * lo.x + lo.y * lo.y + hi.x * hi.x + hi.y * hi.y;
+      sum[0] += lo.x;
+      sum[1] += lo.y;
+      sum[2] += hi.x;
+      sum[3] += hi.y;
+    }
+    const double V = geo[16 * e + 12];
+    acc += V / 20.0 * (sq + sum[0] * sum[0] + sum[1] * sum[1] + sum[2] * sum[2] + sum[3] * sum[3]);
+  }
+  acc = cta_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kNormThreads) sum_partials_kernel(const double* __restrict__ partial, int nblk,
+                                                                  double* __restrict__ out) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) acc += partial[k];
+  acc = cta_sum(acc);
+  if (threadIdx.x == 0) *out = acc;
+}
+
 }  // namespace
 
 void launch_newmark(Handle& h, const double* state, double* disp, double* vel, double* acc, double* hist,
@@ -694,6 +750,13 @@ void launch_assemble_colour(Handle& h, const double* state, const double* hist, 
       FSI_LAUNCH(fsi::KC_OTHER, s, dirichlet_matrix_kernel<double><<<blocks_for(L0.nb, 256), 256, 0, s>>>(L0.nb, L0.block_row, L0.col_idx,
                                                                              h.d_dir_mask, (double*)vals));
   }
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_mass_norm2(Handle& h, const double* x, double* out_dev, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, mass_norm_partial_kernel<<<h.red_blocks, kNormThreads, 0, s>>>(
+      h.n_elems, h.d_conn, h.d_geo, x, h.d_partial));
+  FSI_LAUNCH(fsi::KC_VECTOR, s, sum_partials_kernel<<<1, kNormThreads, 0, s>>>(h.d_partial, h.red_blocks, out_dev));
   FSI_CUDA_TRY(cudaGetLastError());
 }
 

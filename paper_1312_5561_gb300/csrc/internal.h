@@ -230,6 +230,8 @@ void launch_assemble_gather(Handle& h, const double* state, const double* hist, 
 void launch_assemble_colour(Handle& h, const double* state, const double* hist, double* residual,
                             bool want_tangent, cudaStream_t s, void* vals_target, int target_fp32);
 void launch_set_dirichlet_values(Handle& h, double* state, const double* values, cudaStream_t s);
+// out_dev[0] = x^T M x, M = diag[M_1, M_2] the P1 mass matrices (x: [n_nodes][4]; deterministic)
+void launch_mass_norm2(Handle& h, const double* x, double* out_dev, cudaStream_t s);
 void launch_newmark(Handle& h, const double* state, double* disp, double* vel, double* acc, double* hist,
                     double beta, double gamma, double dt, cudaStream_t s);
 

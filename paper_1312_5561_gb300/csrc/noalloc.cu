@@ -1,7 +1,7 @@
 // Allocation-free dot products.
 //
 // fsi_dots_static computes the same deterministic FP64 dot products as the
-// Krylov reduction of the solver (a partial sum per CTA, then a fixed-order
+// Krylov reduction of the solver (304 CTA partial sums, then a fixed-order
 // sum of the partials), but its partial sums live in a file-scope
 // __device__ array instead of memory allocated by a handle.  It exists for
 // callers that may not allocate device memory at all: a coupling driver or
@@ -11,23 +11,20 @@
 // cudaMalloc / cudaFree synchronise the device and stall the other streams.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "fsi_solid.h"
 
 namespace {
 
-constexpr int kBlocks = 256;              // partial sums per vector
+// Partial sums per vector: the solver's reductions split every dot product
+// into 2 x 152 CTA partials (two per SM of a GB300), and so does this call,
+// so its sums are bit-identical to the solver's.
+constexpr int kBlocks = 2 * 152;
 constexpr int kMaxVectors = FSI_DOTS_STATIC_MAX_VECTORS;
 constexpr int kThreads = 256;
-constexpr int kMaxDevices = 64;
 
-// Scratch: one partial sum per CTA and vector (kMaxVectors * kBlocks * 8 B = 64 KiB).
+// Scratch: one partial sum per CTA and vector (kMaxVectors * kBlocks * 8 B = 76 KiB).
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) double g_dots_scratch[kMaxVectors * kBlocks];
-
-double* g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_mutex;
 
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double s[kThreads / 32];
@@ -62,20 +59,15 @@ __global__ void dots_final_kernel(const double* __restrict__ partial, double* __
   if (threadIdx.x == 0) out[i] = acc;
 }
 
-// Device address of the scratch array on the current device (set up once per device).
+// Device address of the scratch array in the current device's current
+// context.  The address belongs to a context, not to a device (it changes
+// after cudaDeviceReset, for instance), so it is looked up on every call; the
+// lookup allocates nothing.
 cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_dots_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_dots_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 

@@ -113,6 +113,15 @@ int check_err(Handle& h, cudaStream_t s) {
   return e;
 }
 
+// sqrt(x^T M x) with the P1 mass matrices (Sec. 4.4, Eq. newstop)
+double mass_norm_host(Handle& h, const double* x, cudaStream_t s) {
+  launch_mass_norm2(h, x, h.d_dots + kDotNorm + 4, s);
+  double v = 0.0;
+  FSI_CUDA_TRY(cudaMemcpyAsync(&v, h.d_dots + kDotNorm + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  return std::sqrt(std::max(v, 0.0));
+}
+
 double norm2_host(Handle& h, const double* x, long n, cudaStream_t s) {
   dots(h, x, 0, 1, x, n, h.d_dots + kDotNorm, s);
   double v = 0.0;
@@ -868,6 +877,7 @@ static int newton_iterate(Handle& h, double* state, const fsi_load* load, double
     info->krylov_its_last = its;
     info->lin_res = rel;
     info->inc_norm = norm2_host(h, h.d_t2, n, s);
+    info->inc_mnorm = mass_norm_host(h, h.d_t2, s);
   }
   (void)rn;
   if (rel > h.opts.krylov_rtol * 1e3 && its >= h.opts.max_krylov) return FSI_ERR_NOT_CONVERGED;
@@ -900,6 +910,7 @@ static int solve_impl(Handle& h, double* state, const fsi_load* load, const doub
   const double r0 = norm2_host(h, h.d_res, n, s);
   double rn = r0;
   info->res0 = r0;
+  if (!std::isfinite(r0)) return FSI_ERR_INVERTED;   // a non-finite state or load
   if (guess) {
     FSI_CUDA_TRY(cudaMemcpyAsync(h.d_state_tmp, state, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     FSI_CUDA_TRY(cudaMemcpyAsync(h.d_t3, guess, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -907,7 +918,7 @@ static int solve_impl(Handle& h, double* state, const fsi_load* load, const doub
     axpy(1.0, h.d_t3, h.d_state_tmp, n, s);
     int st2 = assemble_checked(h, h.d_state_tmp, hist, h.d_t, false, s);
     double rg = st2 ? INFINITY : norm2_host(h, h.d_t, n, s);
-    if (rg <= r0) {
+    if (rg <= r0) {   // false for a non-finite guess: the zero increment is kept
       FSI_CUDA_TRY(cudaMemcpyAsync(state, h.d_state_tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       FSI_CUDA_TRY(cudaMemcpyAsync(h.d_res, h.d_t, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       rn = rg;
@@ -954,6 +965,10 @@ static int solve_impl(Handle& h, double* state, const fsi_load* load, const doub
       return st;
     }
     double rnew = norm2_host(h, h.d_res, n, s);
+    if (!std::isfinite(rnew)) {
+      info->newton_its = k + 1;
+      return FSI_ERR_INVERTED;
+    }
     eps_prev = rnew / std::max(rn, 1e-300);
     rn = rnew;
   }
@@ -1198,6 +1213,11 @@ fsi_status fsi_solid_newton_step(fsi_solid_t hh, double* state, const fsi_load* 
   int st = fsi::assemble_checked(*h, state, load ? load->hist : nullptr, h->d_res, false, s);
   if (st) return (fsi_status)st;
   info->res0 = fsi::norm2_host(*h, h->d_res, n, s);
+  if (!std::isfinite(info->res0)) {
+    fsi::set_error(h, "non-finite residual");
+    info->status = FSI_ERR_INVERTED;
+    return FSI_ERR_INVERTED;
+  }
   st = fsi::newton_iterate(*h, state, load, info->res0, h->opts.krylov_rtol, info, s);
   info->newton_its = 1;
   info->status = st;

@@ -61,18 +61,26 @@ def test_gradients_match_the_oracle(case):
 
 
 def test_adam_step_matches_the_oracle(case):
+    """Four Adam steps on the device against the oracle's Adam with its own
+    moment state: from the second step on the bias corrections 1 - b1^t and
+    1 - b2^t no longer cancel, so a wrong exponent on either side shows."""
     net, sizes, params, X, T = case
-    before = net.get_params()
-    p = _unflat(before, sizes)
-    _, grads = M.loss_and_grads(p, X.astype(np.float64), T.astype(np.float64))
-    net.train_step(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"), lr=1e-3)
-    after = net.get_params()
-    M.adam_step(p, grads, {}, lr=1e-3)
-    gref = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
-    clear = np.abs(gref) > 1e-3 * np.abs(gref).max()   # FP32 cannot fix the sign of tiny gradients
-    assert np.abs(after - _flat(p))[clear].max() <= 1e-6
-    assert np.abs(after - before).max() <= 1e-3 * (1 + 1e-5)
-    net.set_params(before)
+    start = net.get_params()
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    state = {}
+    for step in range(4):
+        before = net.get_params()
+        p = _unflat(before, sizes)
+        _, grads = M.loss_and_grads(p, X.astype(np.float64), T.astype(np.float64))
+        net.train_step(Xd, Td, lr=1e-3)
+        after = net.get_params()
+        M.adam_step(p, grads, state, lr=1e-3)
+        gref = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+        clear = np.abs(gref) > 1e-3 * np.abs(gref).max()   # FP32 cannot fix the sign of tiny gradients
+        assert np.abs(after - _flat(p))[clear].max() <= 1e-6, step
+        assert np.abs(after - before).max() <= 1e-3 * (1 + 1e-5)
+    assert state["t"] == 4
+    net.set_params(start)
 
 
 def test_learned_guess_saves_newton_iterations():

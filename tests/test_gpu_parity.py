@@ -59,14 +59,17 @@ MESHES = {
 }
 
 
+@pytest.mark.parametrize("assembly", [0, 1], ids=["gather", "colour"])
 @pytest.mark.parametrize("name", list(MESHES))
-def test_residual_and_tangent_parity(name):
+def test_residual_and_tangent_parity(name, assembly):
+    """Both assembly paths: element buffers + fixed-order gather (0) and the
+    colour-ordered scatter (1)."""
     mesh = MESHES[name]()
     P = O.Problem(mesh)
     s = _smooth_state(mesh, 3)
     pressure = 1.3 if len(mesh.neu_faces) else 0.0
     from paper_1312_5561_gb300.binding import Load
-    solver = _solver(mesh)
+    solver = _solver(mesh, assembly=assembly)
     R = solver.residual_tangent(_t(s), Load(pressure=pressure)).cpu().numpy()
     R_ref = P.residual(s, P.external_force(pressure))
     scale = np.abs(R_ref).max(axis=1, keepdims=True)
@@ -82,10 +85,11 @@ def test_residual_and_tangent_parity(name):
         assert act.any(axis=1).all() and not act.all()
 
 
-def test_assembly_is_bitwise_deterministic_and_colouring_matches():
+@pytest.mark.parametrize("assembly", [0, 1], ids=["gather", "colour"])
+def test_assembly_is_bitwise_deterministic_and_colouring_matches(assembly):
     mesh = MESHES["tube_artery"]()
     s = _t(_smooth_state(mesh, 5))
-    solver = _solver(mesh)
+    solver = _solver(mesh, assembly=assembly)
     R1 = solver.residual_tangent(s).clone()
     _, _, v1 = solver.bsr()
     R2 = solver.residual_tangent(s).clone()
@@ -370,3 +374,20 @@ def test_inertia_residual_and_tangent_parity():
     rp, ci, vals = solver.bsr()
     Kg = _bsr_to_csr(rp, ci, vals, mesh.n_nodes)
     assert _blockrow_rel_err(Kg, P.tangent(s, hist), mesh.n_nodes) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_newton_step_reports_the_mass_norm_increment(precision):
+    """info.inc_mnorm is ||dv||_M (Sec. 4.4, Eq. newstop) of the update the
+    step applied, and info.inc_norm its Euclidean norm."""
+    from paper_1312_5561_gb300.binding import Load
+    mesh = MESHES["tube_artery"]()
+    P = O.Problem(mesh)
+    s0 = _smooth_state(mesh, 6, amp=0.02, pamp=0.1)
+    solver = _solver(mesh, precision=precision)
+    state = _t(s0)
+    info = solver.newton_step(state, Load(pressure=0.5))
+    dv = state.cpu().numpy() - s0
+    assert abs(info.inc_mnorm - P.mass_norm(dv)) <= 1e-12 * P.mass_norm(dv)
+    assert abs(info.inc_norm - np.linalg.norm(dv)) <= 1e-12 * np.linalg.norm(dv)
+    assert info.inc_mnorm > 0

@@ -50,6 +50,24 @@ def test_adam_first_step_closed_form():
     assert np.allclose(params[0][1], [0.5 - 0.01 * 1e-3 / (1e-3 + 1e-8)])
 
 
+def test_adam_bias_correction_over_many_steps():
+    """Under a constant gradient g the bias-corrected moments are exactly g
+    and g^2 at every step t (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so every
+    step moves a parameter by lr g / (|g| + eps).  A wrong exponent of b1^t or
+    b2^t changes the step size after the first step and fails this."""
+    g = np.array([[0.3, -4.0, 2e-2]])
+    gb = np.array([-0.7])
+    params = [[np.array([[1.0, -2.0, 0.25]]), np.array([0.5])]]
+    st = {}
+    lr, eps = 0.01, 1e-8
+    for t in range(1, 8):
+        w0, b0 = params[0][0].copy(), params[0][1].copy()
+        M.adam_step(params, [[g, gb]], st, lr=lr, b1=0.8, b2=0.95, eps=eps)
+        assert np.allclose(params[0][0] - w0, -lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+        assert np.allclose(params[0][1] - b0, -lr * gb / (np.abs(gb) + eps), rtol=1e-12, atol=0)
+    assert st["t"] == 7
+
+
 def test_training_reduces_loss_on_a_smooth_map():
     rng = np.random.default_rng(3)
     X = rng.uniform(-1, 1, size=(256, 3))

@@ -342,6 +342,73 @@ def test_pressure_load_resultants():
     assert radial > 0 and abs(f[:, 2]).max() < 1e-14
 
 
+def test_linear_nodal_pressure_load_is_the_consistent_p1_load():
+    """A P1-interpolated (linear) pressure on one tilted triangle: each nodal
+    load must equal -n times the integral of N_a P over the face (Sec. 4.2.3,
+    the <g_n, v> term).  The integral is evaluated here independently, by the
+    edge-midpoint rule, which is exact for the quadratic N_a P.  The moment of
+    the load about the face centroid separates this from a lumped load
+    (A/3 P_a per vertex), which has the right resultant but the wrong moment."""
+    from fixtures.meshes import Mesh
+    X = np.array([[0.1, 0.0, 0.2], [1.3, 0.4, 0.0], [0.2, 1.1, 0.5], [0.3, 0.2, -1.0]])
+    tets = np.array([[0, 2, 1, 3]], dtype=np.int32)
+    face = np.array([[0, 1, 2]], dtype=np.int32)      # right-hand normal away from vertex 3
+    m = Mesh(X=X, tets=tets, mat_id=np.zeros(1, np.int32), fibre=np.zeros((1, 2, 3)),
+             dir_mask=np.zeros((4, 4), np.uint8), neu_faces=face, materials=mooney_rivlin())
+    assert O.p1_geometry(X, tets)[1][0] > 0
+    Pn = np.array([0.7, -0.2, 2.5, 9.9])              # value at vertex 3 is off the face
+    f = O.Problem(m).external_force(pressure=1.5, node_pressure=Pn)
+    v = face[0]
+    x = X[v]
+    nvec = np.cross(x[1] - x[0], x[2] - x[0])
+    area = 0.5 * np.linalg.norm(nvec)
+    n_out = nvec / np.linalg.norm(nvec)
+    assert np.dot(n_out, X[3] - x[0]) < 0
+    # midpoint rule: weights area/3 at the three edge midpoints; there N_a is 1/2
+    # on the two vertices of the edge and 0 on the third
+    mids = [(0, 1), (1, 2), (0, 2)]
+    expect = np.zeros((4, 3))
+    for a in range(3):
+        integ = 0.0
+        for (i, j) in mids:
+            Na = 0.5 if a in (i, j) else 0.0
+            Pm = 1.5 * 0.5 * (Pn[v[i]] + Pn[v[j]])
+            integ += area / 3.0 * Na * Pm
+        expect[v[a]] = -n_out * integ
+    assert np.abs(f - expect).max() < 1e-14
+    assert np.abs(f[3]).max() == 0.0
+    # moment about the centroid: -n x-products of int (x - c) P dA, midpoint rule again
+    c = x.mean(axis=0)
+    mom_expect = np.zeros(3)
+    for (i, j) in mids:
+        xm = 0.5 * (x[i] + x[j])
+        Pm = 1.5 * 0.5 * (Pn[v[i]] + Pn[v[j]])
+        mom_expect += area / 3.0 * Pm * np.cross(xm - c, -n_out)
+    mom = sum(np.cross(X[k] - c, f[k]) for k in v)
+    assert np.abs(mom - mom_expect).max() < 1e-13
+    lumped = [-n_out * area / 3.0 * 1.5 * Pn[k] for k in v]
+    mom_lumped = sum(np.cross(X[k] - c, lk) for k, lk in zip(v, lumped))
+    assert np.abs(mom_lumped - mom_expect).max() > 1e-2
+
+
+def test_mass_norm_integrates_fields_exactly():
+    """||v||_M of Sec. 4.4 is the L2 norm of the P1 field: for a constant
+    field it is |c| sqrt(vol), and for a linear field on the unit cube the P1
+    interpolant is exact, so int x^2 dV = 1/3 and int (x + 2y)^2 dV =
+    1/3 + 4/4 + 4/3 = 8/3 (int x y = 1/4)."""
+    m = kuhn_cube(3)
+    P = O.Problem(m)
+    c = np.array([0.3, -1.2, 0.5, 2.0])
+    v = np.tile(c, (m.n_nodes, 1))
+    assert abs(P.mass_norm(v) - np.linalg.norm(c)) < 1e-13
+    v = np.zeros((m.n_nodes, 4))
+    v[:, 0] = m.X[:, 0]
+    assert abs(P.mass_norm(v) ** 2 - 1.0 / 3.0) < 1e-13
+    v[:, 0] = 0.0
+    v[:, 3] = m.X[:, 0] + 2.0 * m.X[:, 1]
+    assert abs(P.mass_norm(v) ** 2 - 8.0 / 3.0) < 1e-13
+
+
 def test_pspg_under_uniform_dilation():
     """With F = lam I and a linear pressure field the PSPG term reduces to
     -tau V lam grad p . g_a (J F^-T grad p . F^-T g_a = lam grad p . g_a)."""
