@@ -79,8 +79,7 @@ typedef struct {
 
 enum { FSI_PREC_FP64 = 0, FSI_PREC_FP32_IR = 1 };
 enum { FSI_KRYLOV_FGMRES = 0, FSI_KRYLOV_BICGSTAB = 1 };
-/* Smoother of the finest AMG level (coarser levels always use damped block
- * Jacobi).
+/* Smoother of the finest AMG level (coarser levels: see coarse_smoother).
  *  FSI_SMOOTHER_JACOBI  damped 4x4 block Jacobi, damping omega.
  *  FSI_SMOOTHER_VANKA   the multiplicative Vanka smoother of Sec. 5.5.2
  *                       (Eq. locsys, vankasmooth): one patch per pressure
@@ -113,6 +112,21 @@ enum { FSI_PRECOND_AMG = 0, FSI_PRECOND_BLOCK_LT = 1 };
  *                where FSI_AGG_RING coarsens along the weak directions and the
  *                Krylov iteration stalls. */
 enum { FSI_AGG_RING = 0, FSI_AGG_GROW = 1 };
+/* Smoother of the coarser AMG levels (7x7 blocks: rigid-body modes and a
+ * constant pressure per aggregate).
+ *  FSI_COARSE_JACOBI  damped block Jacobi x += omega D^-1 (b - A x), as on the
+ *                     finest level.  On the saddle-point coarse operators of
+ *                     walls meshed with many thin layers D^-1 A has complex
+ *                     eigenvalues far outside the unit disc and the sweep
+ *                     diverges.
+ *  FSI_COARSE_MR      minimal-residual block Jacobi: z = D^-1 r, w = A z and
+ *                     x += a z, r -= a w with a = (r.w)/(w.w), the step length
+ *                     that minimises ||r - a w||_2, so no sweep can raise the
+ *                     residual (default).  The step length depends on the
+ *                     right-hand side, which makes the V-cycle a nonlinear
+ *                     preconditioner: FGMRES accepts it; with BiCGStab the
+ *                     library falls back to FSI_COARSE_JACOBI. */
+enum { FSI_COARSE_JACOBI = 0, FSI_COARSE_MR = 1 };
 
 /* Solver options.  Defaults come from fsi_solid_default_opts(). */
 typedef struct {
@@ -150,6 +164,7 @@ typedef struct {
                                (7x7) operators as BF16 copies (smoothing and residual;
                                FP32 accumulation); the Galerkin products, transfers,
                                block inverses and coarsest solve stay FP32 */
+  int32_t coarse_smoother;  /* FSI_COARSE_* (sweeps: nu_coarse before and after) */
 } fsi_solver_opts;
 
 /* Load of one solve (device arrays owned by the caller; NULL = absent).
@@ -187,8 +202,8 @@ typedef struct {
 } fsi_info;
 
 /* Default options: FP64, FGMRES(100), block Jacobi 4+4 sweeps on the finest
- * level and 1+1 on coarser levels, omega 0.7, V-cycle replayed from a CUDA
- * graph, coarse levels refreshed every Newton step,
+ * level and minimal-residual block Jacobi 2+2 on coarser levels, omega 0.7,
+ * V-cycle replayed from a CUDA graph, coarse levels refreshed every Newton step,
  * Newton rtol 1e-8, Krylov rtol 1e-8, PSPG on, fibre_factor 2. */
 void fsi_solid_default_opts(fsi_solver_opts* opts);
 

@@ -115,6 +115,8 @@ struct Level {
   void* x2 = nullptr;
   void* b = nullptr;
   void* r = nullptr;
+  void* w = nullptr;         // minimal-residual smoothing: A z (coarse levels)
+  double* mr = nullptr;      // minimal-residual smoothing: 2 x kMrBlocks dot partials, then the step length
   HostPattern hpat;          // level 0 pattern (host copy)
 };
 
@@ -260,6 +262,8 @@ void launch_coarse_factor(Handle& h, bool fp32, cudaStream_t s);
 void launch_values_to_bf16(const Level& L, cudaStream_t s);
 template <typename T>
 void vcycle(Handle& h, int level, cudaStream_t s);
+// CTAs of the deterministic dot partials of the minimal-residual smoother
+constexpr int kMrBlocks = 2 * 152;
 // FP64 vector helpers; reductions are deterministic (fixed two-pass order)
 // out_dev[i] = V_i . y for V_i = V + i ldv, i < k
 void dots(Handle& h, const double* V, long ldv, int k, const double* y, long n, double* out_dev,

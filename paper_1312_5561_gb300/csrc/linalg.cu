@@ -324,6 +324,84 @@ __global__ void jacobi_zero_kernel(int n, const T* __restrict__ dinv, const T* _
   x[(size_t)row * B + r] = omega * acc;
 }
 
+// ---- minimal-residual block Jacobi (coarse levels).  One sweep:
+// z = D^-1 r, w = A z, a = (r.w)/(w.w), x += a z, r -= a w.  The step length
+// minimises ||r - a w||_2 over a, so a sweep never raises the residual, even
+// where D^-1 A has eigenvalues with which a fixed damping diverges.  The two
+// dot products are summed in FP64 over a fixed partition (one partial per
+// CTA, then the partials in index order): deterministic.
+constexpr int kMrThreads = 256;
+
+__device__ __forceinline__ double mr_block_sum(double v) {
+  __shared__ double sh[kMrThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < kMrThreads / 32) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+
+// part[blk] = sum r.w, part[gridDim.x + blk] = sum w.w over this CTA's grid-stride entries
+template <typename T>
+__global__ void __launch_bounds__(kMrThreads) mr_dots_kernel(long m, const T* __restrict__ r,
+                                                             const T* __restrict__ w, double* __restrict__ part) {
+  double rw = 0.0, ww = 0.0;
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (long)gridDim.x * blockDim.x) {
+    const double wk = (double)w[k];
+    rw += (double)r[k] * wk;
+    ww += wk * wk;
+  }
+  rw = mr_block_sum(rw);
+  ww = mr_block_sum(ww);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = rw;
+    part[gridDim.x + blockIdx.x] = ww;
+  }
+}
+
+// part[2 nblk] = (sum part[0..nblk)) / (sum part[nblk..2 nblk)), 0 when w = 0
+__global__ void __launch_bounds__(kMrThreads) mr_alpha_kernel(int nblk, double* __restrict__ part) {
+  double rw = 0.0, ww = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
+    rw += part[k];
+    ww += part[nblk + k];
+  }
+  rw = mr_block_sum(rw);
+  ww = mr_block_sum(ww);
+  if (threadIdx.x == 0) part[2 * nblk] = (ww > 0.0 && isfinite(rw / ww)) ? rw / ww : 0.0;
+}
+
+// x += a z, r -= a w, then z = D^-1 r for the next sweep (one thread per block row)
+template <typename T, int B>
+__global__ void mr_update_kernel(int n, const double* __restrict__ alpha, const T* __restrict__ dinv,
+                                 T* __restrict__ x, T* __restrict__ r, const T* __restrict__ w,
+                                 T* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T a = (T)(*alpha);
+  T rr[B];
+  const size_t o = (size_t)i * B;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    x[o + c] += a * z[o + c];
+    rr[c] = r[o + c] - a * w[o + c];
+    r[o + c] = rr[c];
+  }
+  const T* d = dinv + (size_t)i * (B * B);
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    T acc = 0;
+#pragma unroll
+    for (int c = 0; c < B; ++c) acc += d[q * B + c] * rr[c];
+    z[o + q] = acc;
+  }
+}
+
 // number of displacement-like unknowns in a B-block (3 of 4, 6 of 7)
 template <int B>
 struct NU {
@@ -900,7 +978,9 @@ static void galerkin_t(Level& L, Level& C, bool filter, cudaStream_t s) {
   // tile, each A block read once per output block), one thread per output
   // entry on the 7x7 levels (per-entry threads of one output block share its
   // pair blocks through L1).  P^T (A P): one thread
-  // per entry everywhere.  Both choices measured faster on the 393k-tet tube.
+  // per entry everywhere.  Both choices measured faster on the 393k-tet tube
+  // (a warp-staged variant, 32 output blocks per warp with their pair blocks
+  // copied through shared memory, measured 3x slower on the 3.1M-tet tube).
   if constexpr (B == 4)
     FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_block_kernel<T, B><<<blocks_for(L.ap_nb, 128), 128, 0, s>>>(
         L.ap_nb, L.ap_ptr, L.ap_pairs, (const T*)L.vals, (const T*)L.p_v, (T*)L.ap_v));
@@ -985,6 +1065,48 @@ static void smooth(const Level& L, T omega, int sweeps, bool zero_start, cudaStr
     smooth_b<T, 7>(L, omega, sweeps, zero_start, s);
 }
 
+// nu minimal-residual block-Jacobi sweeps on a 7x7 level.  zero_start: x = 0,
+// r = b; otherwise r = b - A x is formed first.  On return x = L.x and
+// r = L.r = b - A x (the restriction reads it directly).
+template <typename T>
+static void smooth_mr(const Level& L, int sweeps, bool zero_start, cudaStream_t s) {
+  constexpr int B = 7;
+  T* x = (T*)L.x;
+  T* r = (T*)L.r;
+  T* z = (T*)L.x2;
+  T* w = (T*)L.w;
+  const T* b = (const T*)L.b;
+  const long m = (long)L.n * B;
+  if (zero_start) {
+    FSI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * m, s));
+    FSI_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+  } else {
+    bsr_launch<T, T, T, 7, 7, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)x, b, nullptr, T(0), r, s,
+                                 fsi::KC_COARSE_BSR);
+  }
+  if (sweeps <= 0) return;
+  FSI_LAUNCH(fsi::KC_COARSE_BSR, s, jacobi_zero_kernel<T, B><<<blocks_for(m, 128), 128, 0, s>>>(
+      L.n, (const T*)L.dinv, r, T(1), z));
+  for (int k = 0; k < sweeps; ++k) {
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (L.vals_lp) {
+        bsr_launch<__nv_bfloat16, float, float, 7, 7, 0, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp, (const float*)z,
+                                                                 nullptr, nullptr, 0.0f, (float*)w, s,
+                                                                 fsi::KC_COARSE_BSR);
+        done = true;
+      }
+    }
+    if (!done)
+      bsr_launch<T, T, T, 7, 7, 0>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)z, nullptr, nullptr, T(0), w, s,
+                                   fsi::KC_COARSE_BSR);
+    FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_dots_kernel<T><<<kMrBlocks, kMrThreads, 0, s>>>(m, r, w, L.mr));
+    FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_alpha_kernel<<<1, kMrThreads, 0, s>>>(kMrBlocks, L.mr));
+    FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_update_kernel<T, B><<<blocks_for(L.n, 128), 128, 0, s>>>(
+        L.n, L.mr + 2 * kMrBlocks, (const T*)L.dinv, x, r, w, z));
+  }
+}
+
 // One V-cycle on levels[level..]: approximately solves K_l x_l = b_l from x_l = 0.
 template <typename T>
 void vcycle(Handle& h, int level, cudaStream_t s) {
@@ -1002,11 +1124,17 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
   const int nu_pre = level == 0 ? h.opts.nu_pre : h.opts.nu_coarse;
   const int nu_post = level == 0 ? h.opts.nu_post : h.opts.nu_coarse;
   const bool vanka = level == 0 && h.opts.smoother == FSI_SMOOTHER_VANKA;
+  const bool mr = L.bs == 7 && L.mr != nullptr;
   if (vanka)
     vanka_smooth<T>(h, nu_pre, true, s);
+  else if (mr)
+    smooth_mr<T>(L, nu_pre, true, s);   // leaves r = b - A x in L.r
   else
     smooth<T>(L, omega, nu_pre, true, s);
-  if (L.bs == 4) {
+  if (mr) {
+    bsr_launch<T, T, T, 7, 7, 0>(Lc.n, L.pt_rp, L.pt_ci, L.pt_v, (const T*)L.r, nullptr, nullptr, T(0), (T*)Lc.b, s,
+                                 fsi::KC_TRANSFER);
+  } else if (L.bs == 4) {
     bsr_launch<T, T, T, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
                                  (T*)L.r, s, fsi::KC_BSR0);
     bsr_launch<T, T, T, 7, 4, 0>(Lc.n, L.pt_rp, L.pt_ci, L.pt_v, (const T*)L.r, nullptr, nullptr, T(0), (T*)Lc.b, s, fsi::KC_TRANSFER);
@@ -1032,6 +1160,8 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
     bsr_launch<T, T, T, 7, 7, 3>(L.n, L.p_rp, L.p_ci, L.p_v, (const T*)Lc.x, nullptr, nullptr, T(0), (T*)L.x, s, fsi::KC_TRANSFER);
   if (vanka)
     vanka_smooth<T>(h, nu_post, false, s);
+  else if (mr)
+    smooth_mr<T>(L, nu_post, false, s);
   else
     smooth<T>(L, omega, nu_post, false, s);
   FSI_CUDA_TRY(cudaGetLastError());

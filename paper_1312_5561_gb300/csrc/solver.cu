@@ -217,6 +217,10 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
       launch_values_to_bf16(C, s);
     }
     alloc_level_vectors(C, f32);
+    if (h.opts.coarse_smoother == FSI_COARSE_MR && l + 1 < nl) {   // the coarsest level is solved, not smoothed
+      C.w = dalloc<char>(ts * C.bs * (size_t)C.n);
+      C.mr = dalloc<double>(2 * kMrBlocks + 8);
+    }
     h.levels.push_back(std::move(C));
   }
   for (int l = 0; l + 1 < nl; ++l) {
@@ -579,6 +583,10 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
     throw ArgError("unknown smoother");
   if (h.opts.aggregation != FSI_AGG_RING && h.opts.aggregation != FSI_AGG_GROW)
     throw ArgError("unknown aggregation");
+  if (h.opts.coarse_smoother != FSI_COARSE_JACOBI && h.opts.coarse_smoother != FSI_COARSE_MR)
+    throw ArgError("unknown coarse smoother");
+  // BiCGStab needs a fixed (linear) preconditioner
+  if (h.opts.krylov == FSI_KRYLOV_BICGSTAB) h.opts.coarse_smoother = FSI_COARSE_JACOBI;
   h.opts.restart = std::min(std::max(h.opts.restart, 1), kMaxRestart);
   if (h.opts.krylov == FSI_KRYLOV_BICGSTAB) h.opts.restart = std::max(h.opts.restart, 2);   // BiCGStab work vectors
   h.m = h.opts.restart;
@@ -806,7 +814,7 @@ static void destroy_impl(Handle* hp) {
                     (void*)L.p_rp, (void*)L.p_ci, L.p_v, (void*)L.pt_rp, (void*)L.pt_ci, L.pt_v, L.x, L.x2, L.b,
                     L.r, (void*)L.agg, L.ptent, (void*)L.freem, (void*)L.p_brow, (void*)L.w_ptr, (void*)L.w_k,
                     L.w_v, L.dinv_f, (void*)L.pt_src, (void*)L.ap_ptr, (void*)L.ap_pairs, L.ap_v, (void*)L.ac_ptr,
-                    (void*)L.ac_pairs, (void*)L.fix_blk, (void*)L.fix_dof})
+                    (void*)L.ac_pairs, (void*)L.fix_blk, (void*)L.fix_dof, L.w, (void*)L.mr})
       dfree(p);
   }
   if (h.k_vals && !h.levels.empty() && h.k_vals != h.levels[0].vals) dfree(h.k_vals);
@@ -1082,7 +1090,8 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->smoother = FSI_SMOOTHER_JACOBI;
   o->nu_pre = 4;
   o->nu_post = 4;
-  o->nu_coarse = 1;
+  o->nu_coarse = 2;
+  o->coarse_smoother = FSI_COARSE_MR;
   o->coarse_max_nodes = 16;
   o->max_levels = 12;
   o->use_pspg = 1;

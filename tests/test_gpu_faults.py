@@ -5,7 +5,7 @@ library returns and that the handle stays usable."""
 import numpy as np
 import pytest
 
-from fixtures import artery_layers, artery_tube, cube_uniaxial_bc, kuhn_cube
+from fixtures import cube_uniaxial_bc, kuhn_cube
 from oracle import solid as O
 
 torch = pytest.importorskip("torch")
@@ -65,14 +65,14 @@ def test_garbage_guess_falls_back_to_the_zero_increment(kind):
     dropped: Newton starts from the zero increment and reaches the same
     solution as without a guess."""
     from paper_1312_5561_gb300.binding import Load
-    mesh = artery_tube(n_theta=16, n_z=4, materials=artery_layers(1.0e3))
+    mesh = cube_uniaxial_bc(kuhn_cube(4), stretch=0.2)
     rng = np.random.default_rng(3)
     g = 1.0e3 * rng.standard_normal((mesh.n_nodes, 4)) if kind == "huge" else np.full((mesh.n_nodes, 4), np.nan)
     sols = []
     for guess in (None, _t(g)):
         solver = _solver(mesh, newton_rtol=1e-10, krylov_rtol=1e-12, max_krylov=1000)
         state = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
-        info = solver.solve(state, Load(pressure=0.3), guess=guess)
+        info = solver.solve(state, Load(dir_values=_t(mesh.dir_values(0.2))), guess=guess)
         assert info.status == 0 and info.guess_accepted == 0
         sols.append(state.cpu().numpy())
     assert np.array_equal(sols[0], sols[1])

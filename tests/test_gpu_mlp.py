@@ -78,7 +78,8 @@ def test_adam_step_matches_the_oracle(case):
         gref = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
         clear = np.abs(gref) > 1e-3 * np.abs(gref).max()   # FP32 cannot fix the sign of tiny gradients
         assert np.abs(after - _flat(p))[clear].max() <= 1e-6, step
-        assert np.abs(after - before).max() <= 1e-3 * (1 + 1e-5)
+        if step == 0:   # from zero moments every parameter moves by lr g / (|g| + eps) <= lr
+            assert np.abs(after - before).max() <= 1e-3 * (1 + 1e-5)
     assert state["t"] == 4
     net.set_params(start)
 
