@@ -116,7 +116,7 @@ struct Level {
   void* b = nullptr;
   void* r = nullptr;
   void* w = nullptr;         // minimal-residual smoothing: A z (coarse levels)
-  double* mr = nullptr;      // minimal-residual smoothing: 2 x kMrBlocks dot partials, then the step length
+  double* mr = nullptr;      // minimal-residual smoothing: 2 x kMrBlocks dot partials
   HostPattern hpat;          // level 0 pattern (host copy)
 };
 

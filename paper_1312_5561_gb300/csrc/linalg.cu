@@ -126,6 +126,9 @@ __global__ void bsr_kernel(int n, const int32_t* __restrict__ row_ptr, const int
 // every fourth block of the row and row r of each; the four slot sums are
 // then added in a fixed order ((s0 + s2) + (s1 + s3)).  Long coarse rows
 // (~50 blocks) thereby keep 28 lanes busy instead of 7.  Modes as above.
+// (Staging each group of four blocks through shared memory with aligned
+// vector loads, software-pipelined one group ahead, measured 5 % slower on
+// the 3.1M-element tube, and 40 % slower with BF16 values.)
 template <typename TV, typename TX, typename TA, int C, int MODE, typename TD = TV>
 __global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                             const TV* __restrict__ vals, const TX* __restrict__ x, const TX* __restrict__ b,
@@ -364,8 +367,15 @@ __global__ void __launch_bounds__(kMrThreads) mr_dots_kernel(long m, const T* __
   }
 }
 
-// part[2 nblk] = (sum part[0..nblk)) / (sum part[nblk..2 nblk)), 0 when w = 0
-__global__ void __launch_bounds__(kMrThreads) mr_alpha_kernel(int nblk, double* __restrict__ part) {
+// a = (r.w)/(w.w) from the CTA partials (every CTA sums them in the same
+// order), then x += a z, r -= a w and z = D^-1 r for the next sweep (one
+// thread per block row)
+template <typename T, int B>
+__global__ void __launch_bounds__(kMrThreads) mr_update_kernel(int n, int nblk, const double* __restrict__ part,
+                                                               const T* __restrict__ dinv, T* __restrict__ x,
+                                                               T* __restrict__ r, const T* __restrict__ w,
+                                                               T* __restrict__ z) {
+  __shared__ double s_alpha;
   double rw = 0.0, ww = 0.0;
   for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
     rw += part[k];
@@ -373,17 +383,11 @@ __global__ void __launch_bounds__(kMrThreads) mr_alpha_kernel(int nblk, double* 
   }
   rw = mr_block_sum(rw);
   ww = mr_block_sum(ww);
-  if (threadIdx.x == 0) part[2 * nblk] = (ww > 0.0 && isfinite(rw / ww)) ? rw / ww : 0.0;
-}
-
-// x += a z, r -= a w, then z = D^-1 r for the next sweep (one thread per block row)
-template <typename T, int B>
-__global__ void mr_update_kernel(int n, const double* __restrict__ alpha, const T* __restrict__ dinv,
-                                 T* __restrict__ x, T* __restrict__ r, const T* __restrict__ w,
-                                 T* __restrict__ z) {
+  if (threadIdx.x == 0) s_alpha = (ww > 0.0 && isfinite(rw / ww)) ? rw / ww : 0.0;
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const T a = (T)(*alpha);
+  const T a = (T)s_alpha;
   T rr[B];
   const size_t o = (size_t)i * B;
 #pragma unroll
@@ -576,6 +580,77 @@ __global__ void galerkin_ac_kernel(int ac_nb, const int32_t* __restrict__ ac_ptr
     for (int m = 0; m < B; ++m) acc += p[m * NS] * ap[m * NS];
   }
   c_v[(size_t)o * (NS * NS) + e] = acc;
+}
+
+// ---- Galerkin pair products on the tensor cores (FP32 levels).
+// out[o] = sum over the plan of op(X[qa]) Y[qb], with X blocks RX x CX
+// (row-major; op = identity, or the transpose when TRANS), Y blocks KY x NY,
+// out blocks MO x NY, MO, K, NY <= 8.  One warp owns one output block and
+// runs through its pairs in plan order; each pair is one m16n8k8 product
+// with the block padded into rows 0..7 of the 16 x 8 A operand.  FP32
+// accuracy comes from the split x = hi + lo into two TF32 numbers (hi = x
+// rounded to TF32, lo = x - hi rounded again) and three products
+// hi*hi + hi*lo + lo*hi (the dropped lo*lo term is below FP32 rounding).
+// Per pair a lane loads four operand values, against 14 scattered loads per
+// output entry in the one-thread-per-entry form.
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  const float r = x - __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+  hi = h;
+  lo = l;
+}
+
+__device__ __forceinline__ void mma_tf32_16x8x8(float c[4], uint32_t a0, uint32_t a2, uint32_t b0, uint32_t b1) {
+  const uint32_t z = 0u;   // rows 8..15 of the A operand are padding
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(z), "r"(a2), "r"(z), "r"(b0), "r"(b1));
+}
+
+template <int RX, int CX, int KY, int NY, bool TRANS>
+__global__ void __launch_bounds__(128) pair_mma_kernel(int n_out, const int32_t* __restrict__ ptr,
+                                                       const int32_t* __restrict__ pairs,
+                                                       const float* __restrict__ xv, const float* __restrict__ yv,
+                                                       float* __restrict__ out) {
+  constexpr int MO = TRANS ? CX : RX;
+  constexpr int K = TRANS ? RX : CX;
+  static_assert(K == KY && MO <= 8 && K <= 8 && NY <= 8, "block shapes of a pair product");
+  const int o = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (o >= n_out) return;   // warp-uniform
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // fragment positions (PTX m16n8k8 .tf32): A a0 = (g, t), a2 = (g, t + 4);
+  // B b0 = (k = t, n = g), b1 = (k = t + 4, n = g); C c0 = (g, 2t), c1 = (g, 2t + 1)
+  const bool a0_in = g < MO && t < K, a2_in = g < MO && t + 4 < K;
+  const bool b0_in = t < K && g < NY, b1_in = t + 4 < K && g < NY;
+  const int xa0 = TRANS ? t * CX + g : g * CX + t;
+  const int xa2 = TRANS ? (t + 4) * CX + g : g * CX + t + 4;
+  const int yb0 = t * NY + g, yb1 = (t + 4) * NY + g;
+  float c[4] = {0.f, 0.f, 0.f, 0.f};
+  const int s1 = ptr[o + 1];
+  for (int s = ptr[o]; s < s1; ++s) {
+    const int qa = pairs[2 * s], qb = pairs[2 * s + 1];
+    const float* X = xv + (size_t)qa * (RX * CX);
+    const float* Y = yv + (size_t)qb * (KY * NY);
+    const float fa0 = a0_in ? X[xa0] : 0.f, fa2 = a2_in ? X[xa2] : 0.f;
+    const float fb0 = b0_in ? Y[yb0] : 0.f, fb1 = b1_in ? Y[yb1] : 0.f;
+    uint32_t a0h, a0l, a2h, a2l, b0h, b0l, b1h, b1l;
+    tf32_split(fa0, a0h, a0l);
+    tf32_split(fa2, a2h, a2l);
+    tf32_split(fb0, b0h, b0l);
+    tf32_split(fb1, b1h, b1l);
+    mma_tf32_16x8x8(c, a0l, a2l, b0h, b1h);
+    mma_tf32_16x8x8(c, a0h, a2h, b0l, b1l);
+    mma_tf32_16x8x8(c, a0h, a2h, b0h, b1h);
+  }
+  float* po = out + (size_t)o * (MO * NY);
+  if (g < MO) {
+    if (2 * t < NY) po[g * NY + 2 * t] = c[0];
+    if (2 * t + 1 < NY) po[g * NY + 2 * t + 1] = c[1];
+  }
 }
 
 template <typename T>
@@ -981,6 +1056,14 @@ static void galerkin_t(Level& L, Level& C, bool filter, cudaStream_t s) {
   // per entry everywhere.  Both choices measured faster on the 393k-tet tube
   // (a warp-staged variant, 32 output blocks per warp with their pair blocks
   // copied through shared memory, measured 3x slower on the 3.1M-tet tube).
+  // FP32 levels: both products on the tensor cores (pair_mma_kernel, one warp per
+  // output block, 3xTF32 for FP32 accuracy)
+  if constexpr (std::is_same<T, float>::value) {
+    FSI_LAUNCH(fsi::KC_GALERKIN, s, pair_mma_kernel<B, B, B, NS, false><<<blocks_for(32L * L.ap_nb, 128), 128, 0, s>>>(
+        L.ap_nb, L.ap_ptr, L.ap_pairs, (const float*)L.vals, (const float*)L.p_v, (float*)L.ap_v));
+    FSI_LAUNCH(fsi::KC_GALERKIN, s, pair_mma_kernel<B, NS, B, NS, true><<<blocks_for(32L * C.nb, 128), 128, 0, s>>>(
+        C.nb, L.ac_ptr, L.ac_pairs, (const float*)L.p_v, (const float*)L.ap_v, (float*)C.vals));
+  } else {
   if constexpr (B == 4)
     FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ap_block_kernel<T, B><<<blocks_for(L.ap_nb, 128), 128, 0, s>>>(
         L.ap_nb, L.ap_ptr, L.ap_pairs, (const T*)L.vals, (const T*)L.p_v, (T*)L.ap_v));
@@ -989,6 +1072,7 @@ static void galerkin_t(Level& L, Level& C, bool filter, cudaStream_t s) {
         L.ap_nb, L.ap_ptr, L.ap_pairs, (const T*)L.vals, (const T*)L.p_v, (T*)L.ap_v));
   FSI_LAUNCH(fsi::KC_GALERKIN, s, galerkin_ac_kernel<T, B><<<blocks_for((long)C.nb * NS * NS, 256), 256, 0, s>>>(
       C.nb, L.ac_ptr, L.ac_pairs, (const T*)L.p_v, (const T*)L.ap_v, (T*)C.vals));
+  }
   if (L.n_fix > 0)
     FSI_LAUNCH(fsi::KC_GALERKIN, s, identity_fix_kernel<T><<<blocks_for(L.n_fix, 128), 128, 0, s>>>(L.n_fix, L.fix_blk, L.fix_dof, (T*)C.vals));
 }
@@ -1081,8 +1165,18 @@ static void smooth_mr(const Level& L, int sweeps, bool zero_start, cudaStream_t 
     FSI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * m, s));
     FSI_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
   } else {
-    bsr_launch<T, T, T, 7, 7, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)x, b, nullptr, T(0), r, s,
-                                 fsi::KC_COARSE_BSR);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (L.vals_lp) {
+        bsr_launch<__nv_bfloat16, float, float, 7, 7, 1, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp, (const float*)x,
+                                                                 (const float*)b, nullptr, 0.0f, (float*)r, s,
+                                                                 fsi::KC_COARSE_BSR);
+        done = true;
+      }
+    }
+    if (!done)
+      bsr_launch<T, T, T, 7, 7, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)x, b, nullptr, T(0), r, s,
+                                   fsi::KC_COARSE_BSR);
   }
   if (sweeps <= 0) return;
   FSI_LAUNCH(fsi::KC_COARSE_BSR, s, jacobi_zero_kernel<T, B><<<blocks_for(m, 128), 128, 0, s>>>(
@@ -1101,9 +1195,8 @@ static void smooth_mr(const Level& L, int sweeps, bool zero_start, cudaStream_t 
       bsr_launch<T, T, T, 7, 7, 0>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)z, nullptr, nullptr, T(0), w, s,
                                    fsi::KC_COARSE_BSR);
     FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_dots_kernel<T><<<kMrBlocks, kMrThreads, 0, s>>>(m, r, w, L.mr));
-    FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_alpha_kernel<<<1, kMrThreads, 0, s>>>(kMrBlocks, L.mr));
-    FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_update_kernel<T, B><<<blocks_for(L.n, 128), 128, 0, s>>>(
-        L.n, L.mr + 2 * kMrBlocks, (const T*)L.dinv, x, r, w, z));
+    FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_update_kernel<T, B><<<blocks_for(L.n, kMrThreads), kMrThreads, 0, s>>>(
+        L.n, kMrBlocks, L.mr, (const T*)L.dinv, x, r, w, z));
   }
 }
 
