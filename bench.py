@@ -281,11 +281,13 @@ def run_gpu(args, rank, world, verify_path=None):
     # kernel-timing pass: the same Newton steps continued, with CUDA events recorded
     # on the launching stream around every launch (the V-cycle is then launched
     # kernel by kernel instead of from its graph)
-    solver.kernel_timing(True)
-    for _ in range(args.prof_steps):
-        drv.step()
-    torch.cuda.synchronize()
-    prof = solver.kernel_timing(False)
+    prof = {}
+    if args.prof_steps > 0:
+        solver.kernel_timing(True)
+        for _ in range(args.prof_steps):
+            drv.step()
+        torch.cuda.synchronize()
+        prof = solver.kernel_timing(False)
     ms_total = max_over_ranks(ms_total, world)
     steps_per_s = args.steps / (ms_total * 1e-3)
 
@@ -307,7 +309,7 @@ def run_gpu(args, rank, world, verify_path=None):
     host = torch.zeros((mesh.n_nodes, 4), dtype=torch.float64).pin_memory()
     host.copy_(drv.state.cpu())
     dev = torch.empty_like(drv.state)
-    e_steps = max(3, args.steps // 2)
+    e_steps = max(3, args.steps // 2) if args.e2e_steps < 0 else args.e2e_steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e_steps):
@@ -315,7 +317,7 @@ def run_gpu(args, rank, world, verify_path=None):
         drv.step(dev)
         host.copy_(dev, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    e2e = e_steps / (time.perf_counter() - t0)
+    e2e = e_steps / (time.perf_counter() - t0) if e_steps > 0 else None
     nbytes = mesh.n_nodes * 4 * 8
 
     # the converged first load step, for the oracle's residual check (cpu_baseline leg)
@@ -329,10 +331,10 @@ def run_gpu(args, rank, world, verify_path=None):
                   "pressure": P_MAX / N_LOADS}
 
     L0n, L0nb = levels[0]
-    dominant = max(prof, key=lambda k: prof[k][0])
+    dominant = max(prof, key=lambda k: prof[k][0]) if prof else None
     peaks, src = _peaks()
     roof = None
-    jt, jc = prof["jacobi0"]
+    jt, jc = prof.get("jacobi0", (0.0, 0))
     if jc > 0 and args.smoother != "vanka":   # with Vanka this class holds the patch sweeps
         per_launch_s = jt * 1e-3 / jc
         byt = jacobi0_bytes(L0n, L0nb, prec == 1)
@@ -474,7 +476,9 @@ def main():
     ap.add_argument("--no-golden", action="store_true", help="skip the error against the stored oracle solutions")
     ap.add_argument("--single", action="store_true", help="skip the plain-FP64 comparison run")
     ap.add_argument("--graphs", type=int, default=1, help="replay the V-cycle from a captured CUDA graph")
-    ap.add_argument("--prof-steps", type=int, default=6, help="Newton steps of the kernel-timing pass")
+    ap.add_argument("--prof-steps", type=int, default=6, help="Newton steps of the kernel-timing pass (0: none)")
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="Newton steps of the end-to-end pass (default max(3, steps // 2); 0: none)")
     ap.add_argument("--solver", default="fgmres-amg", choices=["fgmres-amg", "bicgstab-pl"])
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "vanka"])
     ap.add_argument("--nu", type=int, default=1, help="Vanka sweeps before / after the coarse correction")
@@ -562,8 +566,9 @@ def main():
                        krylov_cap_hits_in_timed_steps=res["krylov_cap_hits"],
                        newton_cap_hits_in_timed_steps=res["newton_cap_hits"], amg_levels=res["levels"]),
         "element_tangents_per_s": res["tangents_per_s"] * world,
-        "e2e": {"value": res["e2e_steps_per_s"] * world, "unit": "steps/s",
-                "h2d_bytes_per_step": res["bytes"], "d2h_bytes_per_step": res["bytes"]},
+        "e2e": ({"value": res["e2e_steps_per_s"] * world, "unit": "steps/s",
+                 "h2d_bytes_per_step": res["bytes"], "d2h_bytes_per_step": res["bytes"]}
+                if res["e2e_steps_per_s"] is not None else None),
         "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": res["roofline"],
         "kernel_ms": res["prof"], "dominant_kernel_class": res["dominant"],
         "create_s": round(res["create_s"], 2),

@@ -3,8 +3,9 @@ interface traction.
 
 A per-node MLP (32 features -> 256 -> 256 -> 256 -> 4, tanh, FP32 weights)
 maps the node's reference position, layer, surface flag, the interface
-pressure now and one and two steps ago, the node's own (noisy) traction and
-the node's last two converged increments to the next increment
+pressure now and one and two steps ago, the node's own (noisy) traction now
+and one step ago and the node's last two converged increments to the next
+increment
 (d_x, d_y, d_z, p).  It predicts the correction to the linear extrapolation
 (the previous increment), so the proposal starts from that extrapolation.
 It is trained on the GPU by the library's own forward / backward / Adam
@@ -56,6 +57,7 @@ class StepRecord:
     p_prev: float
     p_prev2: float
     node_p: object         # device FP64 [n]
+    node_p_prev: object    # device FP64 [n], the previous step's nodal traction
     prev_inc: object       # device FP64 [n, 4]
     prev_inc2: object      # device FP64 [n, 4]
     inc: object            # device FP64 [n, 4]
@@ -83,6 +85,7 @@ class TimeLoop:
         self.step_index = 0
         self.p_prev = 0.0
         self.p_prev2 = 0.0
+        self.node_p_prev = z(n)
         self.surface = np.zeros(n, bool)
         self.surface[np.unique(mesh.neu_faces)] = True
 
@@ -92,13 +95,13 @@ class TimeLoop:
         return ramp * pulsatile_pressure(t, self.period)
 
     def snapshot(self):
-        keys = ("state", "disp", "vel", "acc", "hist", "prev_inc", "prev_inc2")
+        keys = ("state", "disp", "vel", "acc", "hist", "prev_inc", "prev_inc2", "node_p_prev")
         return {k: getattr(self, k).clone() for k in keys} | {"step_index": self.step_index, "p_prev": self.p_prev,
                                                              "p_prev2": self.p_prev2,
                                                              "rng": self.rng.bit_generator.state}
 
     def restore(self, snap):
-        for k in ("state", "disp", "vel", "acc", "hist", "prev_inc", "prev_inc2"):
+        for k in ("state", "disp", "vel", "acc", "hist", "prev_inc", "prev_inc2", "node_p_prev"):
             getattr(self, k).copy_(snap[k])
         self.step_index = snap["step_index"]
         self.p_prev = snap["p_prev"]
@@ -114,19 +117,20 @@ class TimeLoop:
         node_p_t = torch.tensor(node_p, device="cuda", dtype=torch.float64)
         guess = None
         if guess_fn is not None:
-            guess = guess_fn(p, self.p_prev, self.p_prev2, node_p_t, self.prev_inc, self.prev_inc2)
+            guess = guess_fn(p, self.p_prev, self.p_prev2, node_p_t, self.node_p_prev, self.prev_inc, self.prev_inc2)
         before = self.state.clone()
         info = self.solver.solve(self.state, B.Load(pressure=1.0, node_pressure=node_p_t, hist=self.hist),
                                  guess=guess)
         inc = self.state - before
-        rec = StepRecord(p, self.p_prev, self.p_prev2, node_p_t, self.prev_inc.clone(), self.prev_inc2.clone(), inc,
-                         info.newton_its)
+        rec = StepRecord(p, self.p_prev, self.p_prev2, node_p_t, self.node_p_prev.clone(), self.prev_inc.clone(),
+                         self.prev_inc2.clone(), inc, info.newton_its)
         self.solver.newmark_advance(self.state, self.disp, self.vel, self.acc, self.hist, self.beta, self.gamma,
                                     self.dt)
         self.prev_inc2 = self.prev_inc
         self.prev_inc = inc
         self.p_prev2 = self.p_prev
         self.p_prev = p
+        self.node_p_prev = node_p_t
         self.step_index = k
         rec.guess_accepted = info.guess_accepted
         return rec
@@ -145,7 +149,7 @@ class GuessModel:
         self.p_scale = 1.0
         self.dp_scale = 1.0
 
-    def features(self, p_now, p_prev, p_prev2, node_p, prev_inc, prev_inc2):
+    def features(self, p_now, p_prev, p_prev2, node_p, node_p_prev, prev_inc, prev_inc2):
         torch = self.torch
         n = self.static.shape[0]
         f = torch.zeros((n, N_FEATURES), device="cuda", dtype=torch.float32)
@@ -157,6 +161,8 @@ class GuessModel:
         f[:, 10] = node_p.float() / self.p_scale
         f[:, 11:15] = prev_inc.float() / self.inc_scale
         f[:, 15:19] = prev_inc2.float() / self.inc_scale
+        f[:, 19] = node_p_prev.float() / self.p_scale
+        f[:, 20] = (node_p - node_p_prev).float() / self.dp_scale
         return f
 
     def fit_scales(self, records):
@@ -173,7 +179,7 @@ class GuessModel:
         X, T = [], []
         for r in records:
             idx = torch.randint(0, self.static.shape[0], (nodes_per_step,), device="cuda", generator=g)
-            f = self.features(r.p_now, r.p_prev, r.p_prev2, r.node_p, r.prev_inc, r.prev_inc2)
+            f = self.features(r.p_now, r.p_prev, r.p_prev2, r.node_p, r.node_p_prev, r.prev_inc, r.prev_inc2)
             X.append(f[idx])
             T.append(((r.inc - r.prev_inc).float() / self.corr_scale)[idx])
         return torch.cat(X).contiguous(), torch.cat(T).contiguous()
@@ -188,8 +194,8 @@ class GuessModel:
             losses.append(self.net.train_step(X[idx].contiguous(), T[idx].contiguous(), lr=lr_t))
         return losses
 
-    def guess(self, p_now, p_prev, p_prev2, node_p, prev_inc, prev_inc2, bf16=True):
-        f = self.features(p_now, p_prev, p_prev2, node_p, prev_inc, prev_inc2)
+    def guess(self, p_now, p_prev, p_prev2, node_p, node_p_prev, prev_inc, prev_inc2, bf16=True):
+        f = self.features(p_now, p_prev, p_prev2, node_p, node_p_prev, prev_inc, prev_inc2)
         y = self.net.forward(f, bf16=bf16)
         return (prev_inc + (y * self.corr_scale).double()).contiguous()
 
@@ -219,7 +225,7 @@ def run_study(mesh, n_steps, n_train, dt=0.01, period=1.0, train_steps=2000, nod
     results = {}
     strategies = {
         "zero": None,
-        "linear_extrapolation": lambda p, pp, pp2, npr, prev, prev2: prev.contiguous(),
+        "linear_extrapolation": lambda p, pp, pp2, npr, npp, prev, prev2: prev.contiguous(),
         "mlp": model.guess,
     }
     for name, fn in strategies.items():
@@ -252,21 +258,28 @@ def main():
     import time
     ap = argparse.ArgumentParser(description="learned Newton initial guess on the two-layer artery")
     ap.add_argument("--nz", type=int, default=128, help="axial hexahedra (128: the 393k-element tube)")
-    # 1600 / 1200: past step ~1690 of this load history Newton degrades and a
-    # Krylov solve stalls (a nearly singular tangent), so 2000 / 1500 does not finish
-    ap.add_argument("--steps", type=int, default=1600, help="time steps (replayed: steps - train)")
-    ap.add_argument("--train", type=int, default=1200, help="time steps whose increments train the MLP")
+    ap.add_argument("--steps", type=int, default=2000, help="time steps (replayed: steps - train)")
+    ap.add_argument("--train", type=int, default=1500, help="time steps whose increments train the MLP")
     ap.add_argument("--train-steps", type=int, default=3000)
+    # Both ends clamped (the paper's tube is fixed at its two ends): with only the
+    # axial component fixed there, the 8-long tube is free to sway sideways, the
+    # per-node noise of the traction pumps its slow bending modes (lateral
+    # displacement up to 0.7 of the radius) and Newton breaks down near step 1690
+    ap.add_argument("--ends", default="clamped", choices=["clamped", "axial"])
     args = ap.parse_args()
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from fixtures import artery_layers, artery_tube
+    from fixtures.meshes import tube_end_bc
     mesh = artery_tube(n_theta=64, n_z=args.nz, length=8.0 * args.nz / 128, materials=artery_layers(1.0e3, rho=1.2))
+    if args.ends == "clamped":
+        mesh = tube_end_bc(mesh, clamped=True)
     t0 = time.time()
     out = run_study(mesh, args.steps, args.train, train_steps=args.train_steps,
                     log=lambda m: print(m, file=sys.stderr, flush=True))
     out["wall_s"] = time.time() - t0
-    out["workload"] = f"artery tube 64x8x{args.nz} ({mesh.n_elems} tets), Newmark beta 0.625 gamma 1 dt 0.01, " \
-                      f"p(t)=1+0.6sin(2pi t)+0.2sin(4pi t)+N(0,0.02^2) per node, {args.steps} steps, train {args.train}"
+    out["workload"] = f"artery tube 64x8x{args.nz} ({mesh.n_elems} tets, ends {args.ends}), Newmark beta 0.625 " \
+                      f"gamma 1 dt 0.01, p(t)=1+0.6sin(2pi t)+0.2sin(4pi t)+N(0,0.02^2) per node, {args.steps} steps, " \
+                      f"train {args.train}"
     print(json.dumps(out))
 
 
