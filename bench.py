@@ -250,6 +250,7 @@ def run_gpu(args, rank, world, verify_path=None):
     solver = SolidSolver(mesh, **opts)
     t_create = time.perf_counter() - t_create
     levels = solver.levels()
+    tuning = solver.tuning()
     drv = RampDriver(solver, mesh.n_nodes, torch, getattr(mesh, "face_pressure", None), opts["max_krylov"],
                      opts["krylov_rtol"])
     for _ in range(args.warmup):
@@ -322,13 +323,21 @@ def run_gpu(args, rank, world, verify_path=None):
 
     # the converged first load step, for the oracle's residual check (cpu_baseline leg)
     verify = None
-    if verify_path is not None and args.config != "batched":
+    if verify_path is not None:
         vstate = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
         vinfo = solver.solve(vstate, drv.load(1), check=False)
-        np.save(verify_path, vstate.cpu().numpy())
+        v = vstate.cpu().numpy()
         verify = {"status": int(vinfo.status), "newton_its": int(vinfo.newton_its),
                   "gpu_rel_res": float(vinfo.res / vinfo.res0) if vinfo.res0 > 0 else 0.0,
                   "pressure": P_MAX / N_LOADS}
+        if args.config == "batched":
+            # the two smallest segments, whose oracle solves take seconds
+            sizes = [sg["n_elems"] for sg in mesh.meta["segments"]]
+            pick = [int(i) for i in np.argsort(sizes)[:2]]
+            np.savez(verify_path + ".npz", **{f"seg{i}": v[mesh.seg_node == i] for i in pick})
+            verify.update(segments=pick, pressure=1.0 / N_LOADS)
+        else:
+            np.save(verify_path, v)
 
     L0n, L0nb = levels[0]
     dominant = max(prof, key=lambda k: prof[k][0]) if prof else None
@@ -353,7 +362,7 @@ def run_gpu(args, rank, world, verify_path=None):
         "prof": {k: [round(v[0], 3), v[1]] for k, v in prof.items()}, "dominant": dominant, "roofline": roof,
         "krylov_per_step": krylov / args.steps, "krylov_cap_hits": cap_hits, "newton_cap_hits": newton_caps,
         "levels": levels, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes, "create_s": t_create,
-        "verify": verify,
+        "verify": verify, "tuning": tuning,
     }
 
 
@@ -414,6 +423,28 @@ t0 = time.perf_counter()
 r0 = float(np.linalg.norm(P.residual(np.zeros((mesh.n_nodes, 4)), fext)))
 r = float(np.linalg.norm(P.residual(v, fext)))
 print(json.dumps({{"oracle_rel_res": r / r0, "r0": r0, "r": r, "s": time.perf_counter() - t0}}))
+"""
+
+
+_SEGMENT_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from fixtures import batched_segment
+from oracle import solid as O
+d = np.load({path!r} + ".npz")
+out = {{}}
+for i in {segments}:
+    mesh, off = batched_segment(i, n_seg={nseg}, seed=4)
+    P = O.Problem(mesh)
+    fext = P.external_force({scale}, face_pressure=mesh.face_pressure)
+    t0 = time.perf_counter()
+    ref, its = P.newton(np.zeros((mesh.n_nodes, 4)), fext=fext, rtol=1e-12)
+    got = d["seg%d" % i]
+    out[str(i)] = {{"n_elems": int(mesh.n_elems), "kappa_ratio": float(mesh.meta["kappa_ratio"]),
+                   "rel_err": float(np.abs(got - ref).max() / np.abs(ref).max()), "oracle_newton_its": int(its),
+                   "oracle_s": time.perf_counter() - t0}}
+print(json.dumps(out))
 """
 
 
@@ -572,6 +603,9 @@ def main():
         "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": res["roofline"],
         "kernel_ms": res["prof"], "dominant_kernel_class": res["dominant"],
         "create_s": round(res["create_s"], 2),
+        "autotuned_launch_shapes": {"element_cta": res["tuning"][0], "levels": res["tuning"][1:],
+                                    "meaning": "level 0: CTA size; coarser levels: 1 = CTA per block row, "
+                                               "2 = warp per block row"},
     }
     if res["krylov_cap_hits"] or res["newton_cap_hits"]:
         out["warning"] = "some timed steps hit the Krylov or Newton cap: not a to-1e-8 number"
@@ -599,11 +633,30 @@ def main():
                      "solutions (tests/golden)"),
             **gold}
     if not args.no_cpu_baseline and world == 1:
-        try:
-            out["cpu_baseline"] = oracle_line(args, 2, 1)
-        except Exception as e:  # the GPU number stands without it
-            out["cpu_baseline"] = {"error": str(e)[-300:]}
-        if verify_path is not None and res["verify"] is not None:
+        if args.config != "batched":
+            try:
+                out["cpu_baseline"] = oracle_line(args, 2, 1)
+            except Exception as e:  # the GPU number stands without it
+                out["cpu_baseline"] = {"error": str(e)[-300:]}
+        if verify_path is not None and res["verify"] is not None and args.config == "batched":
+            try:
+                code = _SEGMENT_SNIPPET.format(root=ROOT, path=verify_path, segments=res["verify"]["segments"],
+                                               nseg=args.nseg, scale=res["verify"]["pressure"])
+                segs = _run_py(code)
+                out["oracle_check"] = dict(res["verify"], segment_errors=segs, what=(
+                    "the GPU's converged first load step of the union mesh against the oracle's Newton solution "
+                    "of each sampled segment alone (max |v - v_oracle| / max |v_oracle|)"))
+                per_elem = sum(v["oracle_s"] / v["oracle_newton_its"] for v in segs.values()) / \
+                    sum(v["n_elems"] for v in segs.values())
+                out["cpu_baseline"] = {
+                    "value": 1.0 / (per_elem * res["n_elems"]), "unit": "steps/s", "cores": 1, "kind": "oracle",
+                    "sample": (f"FP64 oracle Newton steps on the two smallest segments "
+                               f"({', '.join(str(v['n_elems']) for v in segs.values())} elements), time per element "
+                               f"scaled linearly to the {res['n_elems']} elements of the union mesh (an upper bound "
+                               f"on the oracle's rate: its direct solve grows faster than linearly)")}
+            except Exception as e:
+                out["oracle_check"] = {"error": str(e)[-300:]}
+        elif verify_path is not None and res["verify"] is not None:
             try:
                 chk = oracle_residual_check(args, verify_path, res["verify"]["pressure"])
                 out["oracle_check"] = dict(res["verify"], **chk, what=(

@@ -12,6 +12,7 @@ from .meshes import (  # noqa: F401
     mooney_rivlin,
     artery_layers,
     batched_tubes,
+    batched_segment,
     cube_uniaxial_bc,
     tube_end_bc,
 )

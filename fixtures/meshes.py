@@ -331,6 +331,29 @@ def batched_tubes(n_seg=256, seed=4, ne_range=(5.0e3, 2.0e5), n_r=8, dz=8.0 / 12
     return mesh
 
 
+def batched_segment(index, n_seg=256, seed=4, ne_range=(5.0e3, 2.0e5), n_r=8, dz=8.0 / 128):
+    """Segment ``index`` of ``batched_tubes`` (same arguments) as a mesh of its
+    own, in its own frame, with its per-face pressure; also returns the offset
+    of its first node in the union mesh.  Replays the generator's seeded draws
+    up to that segment without building the others."""
+    rng = np.random.default_rng(seed)
+    off_n = 0
+    for s in range(index + 1):
+        ne = math.exp(rng.uniform(math.log(ne_range[0]), math.log(ne_range[1])))
+        n_theta = 32 if ne < 5.0e4 else 64
+        n_z = max(2, int(round(ne / (6 * n_r * n_theta))))
+        alpha = rng.uniform(20.0, 70.0)
+        kratio = math.exp(rng.uniform(math.log(1.0e2), math.log(1.0e5)))
+        pres = rng.uniform(0.5, 2.0)
+        if s < index:
+            off_n += n_theta * (n_r + 1) * (n_z + 1)
+    t = artery_tube(n_theta=n_theta, n_media=n_r // 2, n_adv=n_r - n_r // 2, n_z=n_z, length=n_z * dz,
+                    alpha_deg=(alpha, alpha), materials=artery_layers(kratio))
+    t = dataclasses.replace(t, face_pressure=np.full(len(t.neu_faces), pres))
+    t.meta = dict(t.meta, kappa_ratio=kratio, pressure=pres)
+    return t, off_n
+
+
 def tube_subset(mesh: Mesh, n_elems: int) -> Mesh:
     """The first ``n_elems`` elements of a mesh (axial slab order) re-indexed as
     a mesh of its own; used to bound CPU baselines on large meshes."""

@@ -165,6 +165,11 @@ typedef struct {
                                FP32 accumulation); the Galerkin products, transfers,
                                block inverses and coarsest solve stay FP32 */
   int32_t coarse_smoother;  /* FSI_COARSE_* (sweeps: nu_coarse before and after) */
+  int32_t autotune;         /* 1: at create, time the launch shapes of the element kernel
+                               (CTA of 64 or 128 threads) and of every smoothed level's
+                               block-row kernels (4x4 level: CTA of 64, 128 or 256 threads;
+                               7x7 levels: one CTA or one warp per block row) on this mesh
+                               and keep the fastest (see fsi_solid_get_tuning); 0: defaults */
 } fsi_solver_opts;
 
 /* Load of one solve (device arrays owned by the caller; NULL = absent).
@@ -316,6 +321,14 @@ fsi_status fsi_solid_newmark_advance(fsi_solid_t h, const double* state, double*
 /* Host copy of the element colouring in original element order
  * (colour_out [n_elems]); returns the number of colours in *n_colours. */
 fsi_status fsi_solid_get_colouring(fsi_solid_t h, int32_t* colour_out, int32_t* n_colours);
+
+/* Launch shapes chosen by the autotuner (opts.autotune; project-written, the
+ * paper has no counterpart): out[0] = CTA size of the element kernels,
+ * out[1 + l] = shape of the block-row kernels of level l for every smoothed
+ * level (level 0: CTA size; coarser levels: 1 = one CTA per block row, 2 = one
+ * warp per block row; 0 = the size-based default).  *n_out receives the number
+ * of entries; at most capacity are written (host array). */
+fsi_status fsi_solid_get_tuning(fsi_solid_t h, int32_t* out, int32_t capacity, int32_t* n_out);
 
 /* AMG level sizes: nodes_out[l] for l < *n_levels (host, capacity max_levels). */
 fsi_status fsi_solid_get_levels(fsi_solid_t h, int32_t* nodes_out, int32_t* blocks_out,

@@ -30,6 +30,7 @@ EXPORTS = [
     "fsi_solid_launch_count", "fsi_solid_kernel_timing", "fsi_dots_static",
     "fsi_mlp_create", "fsi_mlp_destroy", "fsi_mlp_num_params", "fsi_mlp_params", "fsi_mlp_forward",
     "fsi_mlp_train_step", "fsi_solid_newmark_advance", "fsi_dn_default_opts", "fsi_solid_dn_solve",
+    "fsi_solid_get_tuning",
 ]
 
 # kernel classes of fsi_solid_kernel_timing (FSI_KC_* in the header)
@@ -59,7 +60,7 @@ class SolverOpts(C.Structure):
                 ("fibre_factor", C.c_double), ("inertia_coef", C.c_double), ("amg_lag", C.c_int32),
                 ("assembly", C.c_int32), ("precond", C.c_int32), ("schur_theta", C.c_double),
                 ("vanka_omega", C.c_double), ("aggregation", C.c_int32), ("coarse_bf16", C.c_int32),
-                ("coarse_smoother", C.c_int32)]
+                ("coarse_smoother", C.c_int32), ("autotune", C.c_int32)]
 
 
 class LoadDesc(C.Structure):
@@ -119,6 +120,8 @@ def _load_library():
     lib.fsi_solid_solve.restype = i32
     lib.fsi_solid_get_colouring.argtypes = [vp, vp, C.POINTER(i32)]
     lib.fsi_solid_get_colouring.restype = i32
+    lib.fsi_solid_get_tuning.argtypes = [vp, vp, i32, C.POINTER(i32)]
+    lib.fsi_solid_get_tuning.restype = i32
     lib.fsi_solid_get_levels.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
     lib.fsi_solid_get_levels.restype = i32
     lib.fsi_solid_last_error.argtypes = [vp]
@@ -310,6 +313,14 @@ class SolidSolver:
         if check:
             self._check(st)
         return info
+
+    def tuning(self):
+        """Launch shapes chosen by the autotuner: [element CTA size, level-0 CTA
+        size, shape of level 1, ...] (see fsi_solid_get_tuning)."""
+        out = np.zeros(64, np.int32)
+        n = C.c_int32()
+        self._check(lib.fsi_solid_get_tuning(self.h, out.ctypes.data, 64, C.byref(n)))
+        return out[:n.value].tolist()
 
     def colouring(self):
         out = np.empty(self.n_elems, np.int32)

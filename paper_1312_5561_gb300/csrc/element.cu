@@ -675,22 +675,23 @@ void launch_assemble_gather(Handle& h, const double* state, const double* hist, 
   void* vals = vals_target ? vals_target : h.k_vals;
   const bool f32 = vals_target ? (target_fp32 == 1) : (h.precision == FSI_PREC_FP32_IR);
   const int ne = h.n_elems;
-  const int nbk = blocks_for(ne, kThreads);
+  const int et = h.elem_threads;
+  const int nbk = blocks_for(ne, et);
   double* er = residual ? h.d_rbuf : nullptr;
   if (want_tangent && f32) {
-    FSI_LAUNCH(fsi::KC_TANGENT, s, element_buffer_kernel<float, float, true><<<nbk, kThreads, 0, s>>>(
+    FSI_LAUNCH(fsi::KC_TANGENT, s, element_buffer_kernel<float, float, true><<<nbk, et, 0, s>>>(
         ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
         (float*)h.d_ebuf, (double*)nullptr, h.d_err));
     if (er)
-      FSI_LAUNCH(fsi::KC_RESIDUAL, s, element_buffer_kernel<double, double, false><<<nbk, kThreads, 0, s>>>(
+      FSI_LAUNCH(fsi::KC_RESIDUAL, s, element_buffer_kernel<double, double, false><<<nbk, et, 0, s>>>(
           ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef,
           h.opts.fibre_factor, (double*)nullptr, er, h.d_err));
   } else if (want_tangent) {
-    FSI_LAUNCH(fsi::KC_TANGENT, s, element_buffer_kernel<double, double, true><<<nbk, kThreads, 0, s>>>(
+    FSI_LAUNCH(fsi::KC_TANGENT, s, element_buffer_kernel<double, double, true><<<nbk, et, 0, s>>>(
         ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
         (double*)h.d_ebuf, er, h.d_err));
   } else if (er) {
-    FSI_LAUNCH(fsi::KC_RESIDUAL, s, element_buffer_kernel<double, double, false><<<nbk, kThreads, 0, s>>>(
+    FSI_LAUNCH(fsi::KC_RESIDUAL, s, element_buffer_kernel<double, double, false><<<nbk, et, 0, s>>>(
         ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, state, hist, h.opts.inertia_coef, h.opts.fibre_factor,
         (double*)nullptr, er, h.d_err));
   }
@@ -757,6 +758,49 @@ void launch_mass_norm2(Handle& h, const double* x, double* out_dev, cudaStream_t
   FSI_LAUNCH(fsi::KC_VECTOR, s, mass_norm_partial_kernel<<<h.red_blocks, kNormThreads, 0, s>>>(
       h.n_elems, h.d_conn, h.d_geo, x, h.d_partial));
   FSI_LAUNCH(fsi::KC_VECTOR, s, sum_partials_kernel<<<1, kNormThreads, 0, s>>>(h.d_partial, h.red_blocks, out_dev));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+// CTA size of the element kernels: 64 or 128 threads (the tangent kernel holds
+// ~220 registers per thread, so the CTA size decides how many CTAs fit on an
+// SM); the tangent of the reference state is timed with each, three
+// repetitions after one warm-up, and the faster is kept.
+void autotune_elements(Handle& h, cudaStream_t s) {
+  const bool f32 = h.precision == FSI_PREC_FP32_IR;
+  double* zero = h.d_state_tmp;
+  FSI_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(double) * 4 * (size_t)h.n_nodes, s));
+  cudaEvent_t e0, e1;
+  FSI_CUDA_TRY(cudaEventCreate(&e0));
+  FSI_CUDA_TRY(cudaEventCreate(&e1));
+  const int ne = h.n_elems;
+  float best = 1e30f;
+  int pick = 128;
+  for (int et : {64, 128}) {
+    auto run = [&]() {
+      if (f32)
+        element_buffer_kernel<float, float, true><<<blocks_for(ne, et), et, 0, s>>>(
+            ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, zero, nullptr, h.opts.inertia_coef,
+            h.opts.fibre_factor, (float*)h.d_ebuf, (double*)nullptr, h.d_err);
+      else
+        element_buffer_kernel<double, double, true><<<blocks_for(ne, et), et, 0, s>>>(
+            ne, h.d_conn, h.d_geo, h.d_fibre, h.d_mat, h.d_mats, zero, nullptr, h.opts.inertia_coef,
+            h.opts.fibre_factor, (double*)h.d_ebuf, (double*)nullptr, h.d_err);
+    };
+    run();
+    FSI_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) run();
+    FSI_CUDA_TRY(cudaEventRecord(e1, s));
+    FSI_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    FSI_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = et;
+    }
+  }
+  h.elem_threads = pick;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   FSI_CUDA_TRY(cudaGetLastError());
 }
 

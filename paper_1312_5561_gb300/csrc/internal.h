@@ -116,6 +116,7 @@ struct Level {
   void* b = nullptr;
   void* r = nullptr;
   void* w = nullptr;         // minimal-residual smoothing: A z (coarse levels)
+  int shape = 0;             // launch shape of this level's block-row kernels (autotuner; 0 = default)
   double* mr = nullptr;      // minimal-residual smoothing: 2 x kMrBlocks dot partials
   HostPattern hpat;          // level 0 pattern (host copy)
 };
@@ -210,6 +211,7 @@ struct Handle {
   void* d_vk_inv = nullptr;      // T [n_nodes][vk_m][vk_m] inverses of the local matrices
   void* d_vk_z = nullptr;        // T [n_nodes][vk_m] local corrections
 
+  int elem_threads = 128;              // CTA size of the element kernels (autotuner)
   cudaStream_t stream = nullptr;
   cudaGraphExec_t vc_exec = nullptr;   // captured V-cycle (use_graphs)
   long long vc_kernels = 0;            // kernels in the captured V-cycle
@@ -258,6 +260,10 @@ void launch_block_inverse(Level& L, bool fp32, int* err, cudaStream_t s);
 // numeric set-up of level+1 from level (smoothed P, P^T, A P, P^T A P)
 void launch_galerkin(Level& L, Level& C, bool fp32, bool filter, cudaStream_t s);
 void launch_coarse_factor(Handle& h, bool fp32, cudaStream_t s);
+// times the launch shapes of every smoothed level's block-row kernels and keeps the fastest
+void autotune_levels(Handle& h, cudaStream_t s);
+// times the CTA size of the element tangent kernel and keeps the fastest (h.elem_threads)
+void autotune_elements(Handle& h, cudaStream_t s);
 // L.vals_lp = bf16(L.vals) (FP32 values, 7x7 blocks)
 void launch_values_to_bf16(const Level& L, cudaStream_t s);
 template <typename T>

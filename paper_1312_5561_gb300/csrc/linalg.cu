@@ -884,12 +884,16 @@ inline int grid_stride_blocks(long n) {
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+// shape: the launch shape chosen by the autotuner for the level (0: default).
+// 7-row blocks: 1 = one CTA per block row (bsr7_cta_kernel), 2 = one warp per
+// block row (bsr7_kernel), 0 = CTA per row below 4096 rows; 4-row blocks: the
+// CTA size (64, 128 or 256; 0 = 128).
 template <typename TV, typename TX, typename TA, int R, int C, int MODE, typename TD = TV>
 static void bsr_launch(int n, const int32_t* rp, const int32_t* ci, const void* vals, const TX* x, const TX* b,
-                       const void* dinv, TA omega, TX* y, cudaStream_t s, int cls) {
+                       const void* dinv, TA omega, TX* y, cudaStream_t s, int cls, int shape = 0) {
   if constexpr (R == 7) {
     if (n == 0) return;
-    if (n < 4096)
+    if (shape == 1 || (shape == 0 && n < 4096))
       FSI_LAUNCH(cls, s, bsr7_cta_kernel<TV, TX, TA, C, MODE, TD><<<n, 224, 0, s>>>(
           n, rp, ci, (const TV*)vals, x, b, (const TD*)dinv, omega, y));
     else
@@ -900,16 +904,19 @@ static void bsr_launch(int n, const int32_t* rp, const int32_t* ci, const void* 
   constexpr int LN = Lanes<R>::v;
   const long threads = (long)n * LN;
   if (threads == 0) return;
-  FSI_LAUNCH(cls, s, bsr_kernel<TV, TX, TA, R, C, MODE><<<blocks_for(threads, 128), 128, 0, s>>>(
+  const int cta = (shape == 64 || shape == 256) ? shape : 128;
+  FSI_LAUNCH(cls, s, bsr_kernel<TV, TX, TA, R, C, MODE><<<blocks_for(threads, cta), cta, 0, s>>>(
       n, rp, ci, (const TV*)vals, x, b, (const TV*)dinv, omega, y));
 }
 
 template <typename T>
 void launch_spmv(const Level& L, const T* x, T* y, cudaStream_t s) {
   if (L.bs == 4)
-    bsr_launch<T, T, T, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, T(0), y, s, fsi::KC_BSR0);
+    bsr_launch<T, T, T, 4, 4, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, T(0), y, s, fsi::KC_BSR0,
+                                 L.shape);
   else
-    bsr_launch<T, T, T, 7, 7, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, T(0), y, s, fsi::KC_COARSE_BSR);
+    bsr_launch<T, T, T, 7, 7, 0>(L.n, L.row_ptr, L.col_idx, L.vals, x, nullptr, nullptr, T(0), y, s,
+                                 fsi::KC_COARSE_BSR, L.shape);
   FSI_CUDA_TRY(cudaGetLastError());
 }
 template void launch_spmv<double>(const Level&, const double*, double*, cudaStream_t);
@@ -1129,12 +1136,13 @@ static void smooth_b(const Level& L, T omega, int sweeps, bool zero_start, cudaS
     if constexpr (B == 7 && std::is_same<T, float>::value) {
       if (L.vals_lp) {
         bsr_launch<__nv_bfloat16, float, float, 7, 7, 2, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp, x, b, L.dinv,
-                                                                 omega, x2, s, fsi::KC_COARSE_BSR);
+                                                                 omega, x2, s, fsi::KC_COARSE_BSR, L.shape);
         std::swap(x, x2);
         continue;
       }
     }
-    bsr_launch<T, T, T, B, B, 2>(L.n, L.row_ptr, L.col_idx, L.vals, x, b, L.dinv, omega, x2, s, (B == 4 ? fsi::KC_JACOBI0 : fsi::KC_COARSE_BSR));
+    bsr_launch<T, T, T, B, B, 2>(L.n, L.row_ptr, L.col_idx, L.vals, x, b, L.dinv, omega, x2, s,
+                                 (B == 4 ? fsi::KC_JACOBI0 : fsi::KC_COARSE_BSR), L.shape);
     std::swap(x, x2);
   }
   // the result must live in L.x
@@ -1170,13 +1178,13 @@ static void smooth_mr(const Level& L, int sweeps, bool zero_start, cudaStream_t 
       if (L.vals_lp) {
         bsr_launch<__nv_bfloat16, float, float, 7, 7, 1, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp, (const float*)x,
                                                                  (const float*)b, nullptr, 0.0f, (float*)r, s,
-                                                                 fsi::KC_COARSE_BSR);
+                                                                 fsi::KC_COARSE_BSR, L.shape);
         done = true;
       }
     }
     if (!done)
       bsr_launch<T, T, T, 7, 7, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)x, b, nullptr, T(0), r, s,
-                                   fsi::KC_COARSE_BSR);
+                                   fsi::KC_COARSE_BSR, L.shape);
   }
   if (sweeps <= 0) return;
   FSI_LAUNCH(fsi::KC_COARSE_BSR, s, jacobi_zero_kernel<T, B><<<blocks_for(m, 128), 128, 0, s>>>(
@@ -1187,13 +1195,13 @@ static void smooth_mr(const Level& L, int sweeps, bool zero_start, cudaStream_t 
       if (L.vals_lp) {
         bsr_launch<__nv_bfloat16, float, float, 7, 7, 0, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp, (const float*)z,
                                                                  nullptr, nullptr, 0.0f, (float*)w, s,
-                                                                 fsi::KC_COARSE_BSR);
+                                                                 fsi::KC_COARSE_BSR, L.shape);
         done = true;
       }
     }
     if (!done)
       bsr_launch<T, T, T, 7, 7, 0>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)z, nullptr, nullptr, T(0), w, s,
-                                   fsi::KC_COARSE_BSR);
+                                   fsi::KC_COARSE_BSR, L.shape);
     FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_dots_kernel<T><<<kMrBlocks, kMrThreads, 0, s>>>(m, r, w, L.mr));
     FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_update_kernel<T, B><<<blocks_for(L.n, kMrThreads), kMrThreads, 0, s>>>(
         L.n, kMrBlocks, L.mr, (const T*)L.dinv, x, r, w, z));
@@ -1229,7 +1237,7 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
                                  fsi::KC_TRANSFER);
   } else if (L.bs == 4) {
     bsr_launch<T, T, T, 4, 4, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
-                                 (T*)L.r, s, fsi::KC_BSR0);
+                                 (T*)L.r, s, fsi::KC_BSR0, L.shape);
     bsr_launch<T, T, T, 7, 4, 0>(Lc.n, L.pt_rp, L.pt_ci, L.pt_v, (const T*)L.r, nullptr, nullptr, T(0), (T*)Lc.b, s, fsi::KC_TRANSFER);
   } else {
     bool done = false;
@@ -1237,13 +1245,13 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
       if (L.vals_lp) {
         bsr_launch<__nv_bfloat16, float, float, 7, 7, 1, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp,
                                                                  (const float*)L.x, (const float*)L.b, nullptr,
-                                                                 0.0f, (float*)L.r, s, fsi::KC_COARSE_BSR);
+                                                                 0.0f, (float*)L.r, s, fsi::KC_COARSE_BSR, L.shape);
         done = true;
       }
     }
     if (!done)
       bsr_launch<T, T, T, 7, 7, 1>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, nullptr, T(0),
-                                   (T*)L.r, s, fsi::KC_COARSE_BSR);
+                                   (T*)L.r, s, fsi::KC_COARSE_BSR, L.shape);
     bsr_launch<T, T, T, 7, 7, 0>(Lc.n, L.pt_rp, L.pt_ci, L.pt_v, (const T*)L.r, nullptr, nullptr, T(0), (T*)Lc.b, s, fsi::KC_TRANSFER);
   }
   vcycle<T>(h, level + 1, s);
@@ -1261,6 +1269,72 @@ void vcycle(Handle& h, int level, cudaStream_t s) {
 }
 template void vcycle<double>(Handle&, int, cudaStream_t);
 template void vcycle<float>(Handle&, int, cudaStream_t);
+
+// ---- autotuner of the block-row launch shapes (create time, once per handle).
+// For every level that is smoothed, the damped block-Jacobi sweep of its own
+// operator (the kernel that dominates the V-cycle) is timed with CUDA events
+// on the handle's stream, three repetitions after one warm-up, for each
+// candidate shape; the fastest is kept in Level::shape.  Candidates: CTA
+// sizes 64, 128, 256 for the 4x4 level; CTA-per-row and warp-per-row kernels
+// for the 7x7 levels.  The vectors are zeroed first (the timing does not
+// depend on the values).
+template <typename T>
+static float time_sweep(Level& L, int shape, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  const T omega = T(0.7);
+  auto run = [&]() {
+    if (L.bs == 4)
+      bsr_launch<T, T, T, 4, 4, 2>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, L.dinv, omega,
+                                   (T*)L.x2, s, fsi::KC_OTHER, shape);
+    else
+      bsr_launch<T, T, T, 7, 7, 2>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)L.x, (const T*)L.b, L.dinv, omega,
+                                   (T*)L.x2, s, fsi::KC_OTHER, shape);
+  };
+  run();
+  FSI_CUDA_TRY(cudaEventRecord(e0, s));
+  for (int r = 0; r < 3; ++r) run();
+  FSI_CUDA_TRY(cudaEventRecord(e1, s));
+  FSI_CUDA_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  FSI_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  return ms;
+}
+
+template <typename T>
+static void autotune_t(Handle& h, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  FSI_CUDA_TRY(cudaEventCreate(&e0));
+  FSI_CUDA_TRY(cudaEventCreate(&e1));
+  const int nl = (int)h.levels.size();
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level& L = h.levels[l];
+    const size_t bytes = sizeof(T) * L.bs * (size_t)L.n;
+    FSI_CUDA_TRY(cudaMemsetAsync(L.x, 0, bytes, s));
+    FSI_CUDA_TRY(cudaMemsetAsync(L.b, 0, bytes, s));
+    const int c4[3] = {64, 128, 256}, c7[2] = {1, 2};
+    const int* cand = L.bs == 4 ? c4 : c7;
+    const int nc = L.bs == 4 ? 3 : 2;
+    float best = 1e30f;
+    int pick = 0;
+    for (int q = 0; q < nc; ++q) {
+      const float ms = time_sweep<T>(L, cand[q], s, e0, e1);
+      if (ms < best) {
+        best = ms;
+        pick = cand[q];
+      }
+    }
+    L.shape = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+void autotune_levels(Handle& h, cudaStream_t s) {
+  if (h.precision == FSI_PREC_FP32_IR)
+    autotune_t<float>(h, s);
+  else
+    autotune_t<double>(h, s);
+  FSI_CUDA_TRY(cudaGetLastError());
+}
 
 void dots(Handle& h, const double* V, long ldv, int k, const double* y, long n, double* out_dev, cudaStream_t s) {
   dim3 grid(h.red_blocks, k);

@@ -799,6 +799,11 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
   h.d_dots = dalloc<double>(kDotSize);
   FSI_CUDA_TRY(cudaMallocHost((void**)&h.h_dots, sizeof(double) * kDotSize));
   FSI_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.opts.autotune) {
+    autotune_elements(h, s);
+    autotune_levels(h, s);
+    if (check_err(h, s)) throw ArgError("reference configuration failed in the autotuning pass");
+  }
   guard.p = nullptr;
   return hp;
 }
@@ -1092,6 +1097,7 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->nu_post = 4;
   o->nu_coarse = 2;
   o->coarse_smoother = FSI_COARSE_MR;
+  o->autotune = 1;
   o->coarse_max_nodes = 16;
   o->max_levels = 12;
   o->use_pspg = 1;
@@ -1300,6 +1306,17 @@ fsi_status fsi_solid_get_colouring(fsi_solid_t hh, int32_t* colour_out, int32_t*
   if (!h) return FSI_ERR_ARG;
   if (colour_out) std::memcpy(colour_out, h->colour_host.data(), sizeof(int32_t) * h->n_elems);
   if (n_colours) *n_colours = h->n_colours;
+  return FSI_OK;
+}
+
+fsi_status fsi_solid_get_tuning(fsi_solid_t hh, int32_t* out, int32_t capacity, int32_t* n_out) {
+  Handle* h = H(hh);
+  if (!h || (capacity > 0 && !out)) return FSI_ERR_ARG;
+  std::vector<int32_t> v;
+  v.push_back(h->elem_threads);
+  for (size_t l = 0; l + 1 < h->levels.size(); ++l) v.push_back(h->levels[l].shape);
+  if (n_out) *n_out = (int32_t)v.size();
+  for (int q = 0; q < capacity && q < (int)v.size(); ++q) out[q] = v[q];
   return FSI_OK;
 }
 

@@ -391,3 +391,24 @@ def test_newton_step_reports_the_mass_norm_increment(precision):
     assert abs(info.inc_mnorm - P.mass_norm(dv)) <= 1e-12 * P.mass_norm(dv)
     assert abs(info.inc_norm - np.linalg.norm(dv)) <= 1e-12 * np.linalg.norm(dv)
     assert info.inc_mnorm > 0
+
+
+def test_autotuner_choices_are_valid_and_keep_the_solution():
+    """The launch shapes the autotuner picks lie in their candidate sets, and
+    the tuned and the default launch shapes give the same Newton solution."""
+    from paper_1312_5561_gb300.binding import Load
+    mesh = artery_tube(n_theta=64, n_z=8, length=0.5, materials=artery_layers(1.0e3))
+    sols = []
+    for tune in (1, 0):
+        solver = _solver(mesh, precision=1, autotune=tune, newton_rtol=1e-10, krylov_rtol=1e-10, max_krylov=600)
+        t = solver.tuning()
+        assert len(t) == len(solver.levels())          # element CTA + every smoothed level
+        if tune:
+            assert t[0] in (64, 128) and t[1] in (64, 128, 256) and all(v in (1, 2) for v in t[2:])
+        else:
+            assert t[0] == 128 and all(v == 0 for v in t[1:])
+        state = torch.zeros((mesh.n_nodes, 4), device="cuda", dtype=torch.float64)
+        info = solver.solve(state, Load(pressure=0.16))
+        assert info.status == 0
+        sols.append(state.cpu().numpy())
+    assert np.abs(sols[0] - sols[1]).max() <= 1e-8 * np.abs(sols[1]).max()

@@ -71,3 +71,21 @@ def test_bench_reference_arm_prints_the_contract_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in line["config"]
+
+
+def test_batched_segment_reproduces_the_union_mesh_segment():
+    """batched_segment(i) rebuilds segment i of batched_tubes alone: same
+    connectivity (shifted by the node offset), fibres, masks, face pressures and
+    coordinates up to the x shift that keeps the segments apart."""
+    from fixtures import batched_segment, batched_tubes
+    m = batched_tubes(n_seg=5, seed=4)
+    for i in range(5):
+        t, off = batched_segment(i, n_seg=5, seed=4)
+        nodes = np.flatnonzero(m.seg_node == i)
+        assert nodes[0] == off and len(nodes) == t.n_nodes
+        em = m.seg_elem == i
+        assert np.array_equal(m.tets[em] - off, t.tets)
+        assert np.array_equal(m.dir_mask[nodes], t.dir_mask)
+        assert np.allclose(m.fibre[em], t.fibre)
+        assert np.allclose(m.face_pressure[m.seg_face == i], t.face_pressure)
+        assert np.allclose(m.X[nodes, 1:], t.X[:, 1:]) and np.allclose(np.ptp(m.X[nodes, 0] - t.X[:, 0]), 0.0)
