@@ -155,9 +155,20 @@ def job_value(steps_per_s_max_time, world):
 
 # ------------------------------------------------------------------ GPU arm
 # DRAM bytes (read + write) per launch of the finest-level block-Jacobi sweep
-# from an ncu capture of that kernel on the same workload (FP32 values); the
-# entry is removed whenever the kernel changes.
-JACOBI0_TRAFFIC = {("tube", 128, "fp32"): 79_937_664}
+# from ncu captures of that kernel (FP32 values); the entry is removed whenever
+# the kernel changes.  393k tube: captured on the workload itself.  3.1M tube:
+# captured on the same tube shortened to 64 axial cells (2,038,144 blocks,
+# 156.77 MB per launch = 1.011 x its algorithmic bytes) and scaled by the block
+# count to 8,108,416 blocks (traffic grows in proportion to the blocks).
+JACOBI0_TRAFFIC = {("tube", 128, "fp32"): 79_937_664, ("refined", 128, "fp32"): 623_688_583}
+
+
+def level1_spmv_bytes(n, nb, fp32, bf16=False):
+    """Algorithmic bytes of one w = A z product on AMG level 1 (7x7 blocks):
+    values + column index per block, row pointer, z read and w written once."""
+    vb = 2 if bf16 else (4 if fp32 else 8)
+    xb = 4 if fp32 else 8
+    return nb * (49 * vb + 4) + (n + 1) * 4 + 2 * n * 7 * xb
 
 
 def jacobi0_bytes(n, nb, fp32):
@@ -342,24 +353,43 @@ def run_gpu(args, rank, world, verify_path=None):
     L0n, L0nb = levels[0]
     dominant = max(prof, key=lambda k: prof[k][0]) if prof else None
     peaks, src = _peaks()
-    roof = None
+    timing = (f"CUDA events around each launch over a {args.prof_steps}-step kernel-timing pass following the "
+              f"timed region (same workload, V-cycle launched eagerly)")
+    roofs = {}
     jt, jc = prof.get("jacobi0", (0.0, 0))
     if jc > 0 and args.smoother != "vanka":   # with Vanka this class holds the patch sweeps
         per_launch_s = jt * 1e-3 / jc
         byt = jacobi0_bytes(L0n, L0nb, prec == 1)
         ach = byt / per_launch_s / 1e9
-        roof = {"kernel": "bsr_kernel<...,4,4,MODE=2> (finest-level block-Jacobi sweep)", "bound": "hbm",
-                "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(ach / peaks["hbm_gbs"], 3),
-                "traffic": JACOBI0_TRAFFIC.get((args.config, args.nz, args.precision)), "peak_source": src,
-                "bytes_per_launch": int(byt), "avg_launch_us": round(per_launch_s * 1e6, 2),
-                "timing": f"CUDA events around each launch over a {args.prof_steps}-step kernel-timing pass "
-                          f"following the timed region (same workload, V-cycle launched eagerly)"}
+        roofs["jacobi0"] = (jt, {
+            "kernel": "bsr_kernel<...,4,4,MODE=2> (finest-level block-Jacobi sweep)", "bound": "hbm",
+            "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach / peaks["hbm_gbs"], 3),
+            "traffic": JACOBI0_TRAFFIC.get((args.config, args.nz, args.precision)), "peak_source": src,
+            "bytes_per_launch": int(byt), "avg_launch_us": round(per_launch_s * 1e6, 2),
+            "class_ms_per_step": round(jt / args.prof_steps, 2), "timing": timing})
+    lt, lc = prof.get("level1_spmv", (0.0, 0))
+    if lc > 0 and len(levels) > 1:
+        per_launch_s = lt * 1e-3 / lc
+        L1n, L1nb = levels[1]
+        byt = level1_spmv_bytes(L1n, L1nb, prec == 1, bool(args.coarse_bf16))
+        ach = byt / per_launch_s / 1e9
+        roofs["level1_spmv"] = (lt, {
+            "kernel": "bsr7_kernel<...,7,MODE=0> (w = A z on AMG level 1 in the minimal-residual sweeps)",
+            "bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach / peaks["hbm_gbs"], 3), "traffic": None, "peak_source": src,
+            "bytes_per_launch": int(byt), "avg_launch_us": round(per_launch_s * 1e6, 2),
+            "class_ms_per_step": round(lt / args.prof_steps, 2), "timing": timing})
+    # the line's roofline is the kernel with the larger share of the step; the other is reported beside it
+    order = sorted(roofs.values(), key=lambda v: -v[0])
+    roof = order[0][1] if order else None
+    roof_other = order[1][1] if len(order) > 1 else None
     solver.close()
     return {
         "steps_per_s": steps_per_s, "ms_per_step": ms_total / args.steps, "tangents_per_s": tangents_per_s,
         "e2e_steps_per_s": e2e, "bytes": nbytes, "launches": launches, "clocks": clk,
         "prof": {k: [round(v[0], 3), v[1]] for k, v in prof.items()}, "dominant": dominant, "roofline": roof,
+        "roofline_other": roof_other,
         "krylov_per_step": krylov / args.steps, "krylov_cap_hits": cap_hits, "newton_cap_hits": newton_caps,
         "levels": levels, "n_elems": mesh.n_elems, "n_nodes": mesh.n_nodes, "create_s": t_create,
         "verify": verify, "tuning": tuning,
@@ -601,6 +631,7 @@ def main():
                  "h2d_bytes_per_step": res["bytes"], "d2h_bytes_per_step": res["bytes"]}
                 if res["e2e_steps_per_s"] is not None else None),
         "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": res["roofline"],
+        "roofline_second_kernel": res["roofline_other"],
         "kernel_ms": res["prof"], "dominant_kernel_class": res["dominant"],
         "create_s": round(res["create_s"], 2),
         "autotuned_launch_shapes": {"element_cta": res["tuning"][0], "levels": res["tuning"][1:],

@@ -347,6 +347,8 @@ enum {
   FSI_KC_COARSE,       /* dense coarsest-level factorisation and solve */
   FSI_KC_VECTOR,       /* Krylov vector kernels and reductions */
   FSI_KC_OTHER,
+  FSI_KC_LEVEL1_SPMV,  /* w = A z on AMG level 1 inside the minimal-residual sweeps
+                          (the coarse-level product with the most bytes) */
   FSI_KC_COUNT
 };
 

@@ -35,7 +35,7 @@ EXPORTS = [
 
 # kernel classes of fsi_solid_kernel_timing (FSI_KC_* in the header)
 KERNEL_CLASSES = ["tangent", "residual", "jacobi0", "bsr0", "coarse_bsr", "transfer", "galerkin", "blockinv",
-                  "coarse", "vector", "other"]
+                  "coarse", "vector", "other", "level1_spmv"]
 
 
 class MeshDesc(C.Structure):

@@ -26,6 +26,7 @@ enum KernelClass {
   KC_COARSE,          // dense coarsest-level factorisation and solve
   KC_VECTOR,          // Krylov vector kernels and reductions
   KC_OTHER,
+  KC_LEVEL1_SPMV,     // w = A z on level 1 inside the minimal-residual sweeps
   KC_COUNT
 };
 struct Profiler {
@@ -117,6 +118,7 @@ struct Level {
   void* r = nullptr;
   void* w = nullptr;         // minimal-residual smoothing: A z (coarse levels)
   int shape = 0;             // launch shape of this level's block-row kernels (autotuner; 0 = default)
+  int kc_spmv = 4;           // launch class of w = A z in the minimal-residual sweeps (KC_COARSE_BSR or KC_LEVEL1_SPMV)
   double* mr = nullptr;      // minimal-residual smoothing: 2 x kMrBlocks dot partials
   HostPattern hpat;          // level 0 pattern (host copy)
 };

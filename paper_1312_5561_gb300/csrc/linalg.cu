@@ -142,28 +142,9 @@ __global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const in
     const int k1 = row_ptr[row + 1];
     int k = row_ptr[row] + j;
     if constexpr (C == R) {
-      // four blocks per slot and step: all their loads are issued before the products
-      for (; k + 12 < k1; k += 16) {
-        int j4[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) j4[u] = col_idx[k + 4 * u];
-        TA v[4][C], y[4][C];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const TV* a = vals + (size_t)(k + 4 * u) * (R * C) + r * C;
-          const TX* xx = x + (size_t)j4[u] * C;
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            v[u][c] = (TA)a[c];
-            y[u][c] = (TA)xx[c];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int c = 0; c < C; ++c) acc += v[u][c] * y[u][c];
-      }
-      // two blocks per slot and step for the rest
+      // two blocks per slot and step: both blocks' loads are issued before the products
+      // (four blocks per slot, or prefetching the next pair in the Galerkin products,
+      // measured no faster)
       for (; k + 4 < k1; k += 8) {
         const TV* a0 = vals + (size_t)k * (R * C) + r * C;
         const TV* a1 = vals + (size_t)(k + 4) * (R * C) + r * C;
@@ -651,22 +632,13 @@ __global__ void __launch_bounds__(128) pair_mma_kernel(int n_out, const int32_t*
   const int xa2 = TRANS ? (t + 4) * CX + g : g * CX + t + 4;
   const int yb0 = t * NY + g, yb1 = (t + 4) * NY + g;
   float c[4] = {0.f, 0.f, 0.f, 0.f};
-  const int s0 = ptr[o], s1 = ptr[o + 1];
-  // software pipeline: the operands of pair s + 1 are loaded while pair s is multiplied
-  float na0 = 0.f, na2 = 0.f, nb0 = 0.f, nb1 = 0.f;
-  auto fetch = [&](int s) {
+  const int s1 = ptr[o + 1];
+  for (int s = ptr[o]; s < s1; ++s) {
     const int qa = pairs[2 * s], qb = pairs[2 * s + 1];
     const float* X = xv + (size_t)qa * (RX * CX);
     const float* Y = yv + (size_t)qb * (KY * NY);
-    na0 = a0_in ? X[xa0] : 0.f;
-    na2 = a2_in ? X[xa2] : 0.f;
-    nb0 = b0_in ? Y[yb0] : 0.f;
-    nb1 = b1_in ? Y[yb1] : 0.f;
-  };
-  if (s0 < s1) fetch(s0);
-  for (int s = s0; s < s1; ++s) {
-    const float fa0 = na0, fa2 = na2, fb0 = nb0, fb1 = nb1;
-    if (s + 1 < s1) fetch(s + 1);
+    const float fa0 = a0_in ? X[xa0] : 0.f, fa2 = a2_in ? X[xa2] : 0.f;
+    const float fb0 = b0_in ? Y[yb0] : 0.f, fb1 = b1_in ? Y[yb1] : 0.f;
     uint32_t a0h, a0l, a2h, a2l, b0h, b0l, b1h, b1l;
     tf32_split(fa0, a0h, a0l);
     tf32_split(fa2, a2h, a2l);
@@ -1224,14 +1196,14 @@ static void smooth_mr(const Level& L, int sweeps, bool zero_start, cudaStream_t 
     if constexpr (std::is_same<T, float>::value) {
       if (L.vals_lp) {
         bsr_launch<__nv_bfloat16, float, float, 7, 7, 0, float>(L.n, L.row_ptr, L.col_idx, L.vals_lp, (const float*)z,
-                                                                 nullptr, nullptr, 0.0f, (float*)w, s,
-                                                                 fsi::KC_COARSE_BSR, L.shape);
+                                                                 nullptr, nullptr, 0.0f, (float*)w, s, L.kc_spmv,
+                                                                 L.shape);
         done = true;
       }
     }
     if (!done)
       bsr_launch<T, T, T, 7, 7, 0>(L.n, L.row_ptr, L.col_idx, L.vals, (const T*)z, nullptr, nullptr, T(0), w, s,
-                                   fsi::KC_COARSE_BSR, L.shape);
+                                   L.kc_spmv, L.shape);
     FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_dots_kernel<T><<<kMrBlocks, kMrThreads, 0, s>>>(m, r, w, L.mr));
     FSI_LAUNCH(fsi::KC_COARSE_BSR, s, mr_update_kernel<T, B><<<blocks_for(L.n, kMrThreads), kMrThreads, 0, s>>>(
         L.n, kMrBlocks, L.mr, (const T*)L.dinv, x, r, w, z));

@@ -217,6 +217,7 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
       launch_values_to_bf16(C, s);
     }
     alloc_level_vectors(C, f32);
+    C.kc_spmv = l == 1 ? KC_LEVEL1_SPMV : KC_COARSE_BSR;
     if (h.opts.coarse_smoother == FSI_COARSE_MR && l + 1 < nl) {   // the coarsest level is solved, not smoothed
       C.w = dalloc<char>(ts * C.bs * (size_t)C.n);
       C.mr = dalloc<double>(2 * kMrBlocks + 8);
