@@ -128,7 +128,10 @@ __global__ void bsr_kernel(int n, const int32_t* __restrict__ row_ptr, const int
 // (~50 blocks) thereby keep 28 lanes busy instead of 7.  Modes as above.
 // (Staging each group of four blocks through shared memory with aligned
 // vector loads, software-pipelined one group ahead, measured 5 % slower on
-// the 3.1M-element tube, and 40 % slower with BF16 values.)
+// the 3.1M-element tube, and 40 % slower with BF16 values; a warp that
+// streams the row's values with coalesced scalar loads and keeps one running
+// sum per lane position lost to the CTA-per-row kernel in the autotuner on
+// every coarse level of that tube.)
 template <typename TV, typename TX, typename TA, int C, int MODE, typename TD = TV>
 __global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                             const TV* __restrict__ vals, const TX* __restrict__ x, const TX* __restrict__ b,
@@ -200,84 +203,6 @@ __global__ void bsr7_kernel(int n, const int32_t* __restrict__ row_ptr, const in
       TA corr = 0;
 #pragma unroll
       for (int c = 0; c < R; ++c) corr += (TA)d[c] * rr[c];
-      y[o] = (TX)((TA)x[o] + omega * corr);
-    }
-  }
-}
-
-// 7x7-block rows read as a stream.  One warp per block row; 28 lanes walk the
-// row's values (contiguous in memory) four blocks at a time, lane l taking
-// values l + 28 q, q = 0..6, of the 196-value group, so every load
-// instruction reads 28 consecutive values (one or two cache lines) instead of
-// seven strided rows of four blocks.  Because 28 is a multiple of 7, lane l
-// always multiplies column c = l mod 7 of its blocks, so it needs one x value
-// per block (x[col * 7 + c], 7 consecutive values across the lanes), and the
-// block row r and block b of its q-th value are the same in every group: the
-// lane keeps one running sum per q over the whole row.  At the end the 196
-// sums go through shared memory and lane r < 7 adds the 28 that belong to row
-// r in a fixed order (deterministic).  Modes as in bsr_kernel.
-template <typename TV, typename TX, typename TA, int MODE, typename TD = TV>
-__global__ void __launch_bounds__(128) bsr7s_kernel(int n, const int32_t* __restrict__ row_ptr,
-                                                    const int32_t* __restrict__ col_idx,
-                                                    const TV* __restrict__ vals, const TX* __restrict__ x,
-                                                    const TX* __restrict__ b, const TD* __restrict__ dinv, TA omega,
-                                                    TX* __restrict__ y) {
-  constexpr int R = 7, BB = 49, G = 4, L = 28;
-  __shared__ TA red[4][G * BB];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (row >= n) return;   // warp-uniform
-  const bool act = lane < L;
-  const int c = lane % R;
-  const int k0 = row_ptr[row], k1 = row_ptr[row + 1];
-  TA sq[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) sq[q] = TA(0);
-  for (int kg = k0; kg < k1; kg += G) {
-    const long lim = (long)(k1 - kg) * BB;   // values of this group that belong to the row
-    TA xv[G];
-#pragma unroll
-    for (int u = 0; u < G; ++u) xv[u] = (kg + u < k1) ? (TA)x[(size_t)col_idx[kg + u] * R + c] : TA(0);
-    const TV* base = vals + (size_t)kg * BB;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int e = lane + L * q;
-      if (act && e < lim) {
-        const int blk = e / BB;
-        const TA xb = blk == 0 ? xv[0] : (blk == 1 ? xv[1] : (blk == 2 ? xv[2] : xv[3]));
-        sq[q] += (TA)base[e] * xb;
-      }
-    }
-  }
-  if (act)
-#pragma unroll
-    for (int q = 0; q < R; ++q) red[w][lane + L * q] = sq[q];
-  __syncwarp();
-  TA acc = 0;
-  if (lane < R) {
-#pragma unroll
-    for (int u = 0; u < G; ++u)
-#pragma unroll
-      for (int cc = 0; cc < R; ++cc) acc += red[w][u * BB + lane * R + cc];
-  }
-  const bool out = lane < R;
-  const size_t o = (size_t)row * R + lane;
-  if constexpr (MODE == 0) {
-    if (out) y[o] = (TX)acc;
-  } else if constexpr (MODE == 1) {
-    if (out) y[o] = (TX)((TA)b[o] - acc);
-  } else if constexpr (MODE == 3) {
-    if (out) y[o] = (TX)((TA)y[o] + acc);
-  } else {
-    const TA res = out ? (TA)b[o] - acc : (TA)0;
-    TA rr[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) rr[q] = __shfl_sync(0xffffffffu, res, q);
-    if (out) {
-      const TD* d = dinv + (size_t)row * (R * R) + lane * R;
-      TA corr = 0;
-#pragma unroll
-      for (int q = 0; q < R; ++q) corr += (TA)d[q] * rr[q];
       y[o] = (TX)((TA)x[o] + omega * corr);
     }
   }
@@ -975,9 +900,6 @@ static void bsr_launch(int n, const int32_t* rp, const int32_t* ci, const void* 
     if (n == 0) return;
     if (shape == 1 || (shape == 0 && n < 4096))
       FSI_LAUNCH(cls, s, bsr7_cta_kernel<TV, TX, TA, C, MODE, TD><<<n, 224, 0, s>>>(
-          n, rp, ci, (const TV*)vals, x, b, (const TD*)dinv, omega, y));
-    else if constexpr (C == 7)
-      FSI_LAUNCH(cls, s, bsr7s_kernel<TV, TX, TA, MODE, TD><<<blocks_for((long)n * 32, 128), 128, 0, s>>>(
           n, rp, ci, (const TV*)vals, x, b, (const TD*)dinv, omega, y));
     else
       FSI_LAUNCH(cls, s, bsr7_kernel<TV, TX, TA, C, MODE, TD><<<blocks_for((long)n * 32, 128), 128, 0, s>>>(
