@@ -86,6 +86,8 @@ def solver_options(args):
         kry.update(smoother=1, vanka_omega=0.86, nu_pre=args.nu, nu_post=args.nu)
     if args.coarse_jacobi:
         kry.update(coarse_smoother=0, nu_coarse=1)
+    if args.nu_finest > 0 and args.smoother != "vanka":
+        kry.update(nu_pre=args.nu_finest, nu_post=args.nu_finest)
     return dict(precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=int(args.graphs),
                 amg_lag=int(args.amg_lag), **kry)
 
@@ -544,6 +546,8 @@ def main():
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "vanka"])
     ap.add_argument("--nu", type=int, default=1, help="Vanka sweeps before / after the coarse correction")
     ap.add_argument("--coarse-bf16", type=int, default=0, help="BF16 coarse-level operators in the V-cycle")
+    ap.add_argument("--nu-finest", type=int, default=0,
+                    help="block-Jacobi sweeps before / after on the finest level (0: the library default, 4)")
     ap.add_argument("--coarse-jacobi", action="store_true",
                     help="damped block Jacobi (1+1) on the coarse levels instead of minimal-residual block Jacobi")
     ap.add_argument("--aggregation", default=None, choices=["ring", "grow"],
@@ -618,7 +622,8 @@ def main():
                        solver=("BiCGStab + block-triangular P_L (AMG V-cycle on A)" if args.solver == "bicgstab-pl"
                                else "FGMRES(100) + AMG V-cycle on K"),
                        finest_smoother=(f"Vanka, {args.nu}+{args.nu} sweeps, omega 0.86" if args.smoother == "vanka"
-                                        else "damped block Jacobi, 4+4 sweeps, omega 0.7"),
+                                        else f"damped block Jacobi, {args.nu_finest or 4}+{args.nu_finest or 4} "
+                                             f"sweeps, omega 0.7"),
                        coarse_smoother=("damped block Jacobi 1+1" if args.coarse_jacobi or args.solver == "bicgstab-pl"
                                         else "minimal-residual block Jacobi 2+2"),
                        coarse_operators="BF16 (V-cycle reads)" if args.coarse_bf16 else "FP32",
