@@ -55,6 +55,17 @@ def test_bench_byte_model_of_the_block_jacobi_sweep():
     assert bench.jacobi0_bytes(74304, 1044160, False) == 1044160 * 132 + 4 * 74305 + 74304 * 224
 
 
+def test_bench_byte_model_of_the_level1_product():
+    """The second roofline numerator: n_b (49 v + 4) + 4 (n + 1) + 2 * 7 n x
+    bytes per w = A z on level 1 (v, x: bytes per value and per vector entry),
+    988,479,044 for the 3.1M tube's level 1 (69,904 rows, 4,921,424 blocks)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.level1_spmv_bytes(69904, 4921424, True) == 4921424 * 200 + 4 * 69905 + 14 * 69904 * 4 == 988479044
+    assert bench.level1_spmv_bytes(69904, 4921424, False) == 4921424 * 396 + 4 * 69905 + 14 * 69904 * 8
+    assert bench.level1_spmv_bytes(69904, 4921424, True, bf16=True) == 4921424 * 102 + 4 * 69905 + 14 * 69904 * 4
+
+
 def test_bench_reference_arm_prints_the_contract_line():
     """`bench.py --impl reference` times the oracle on the host and prints one
     JSON line with the contract's keys (no GPU involved)."""
@@ -71,6 +82,8 @@ def test_bench_reference_arm_prints_the_contract_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in line["config"]
+    # the reported steps at the reported time per step fit in what the arm ran
+    assert line["steps"] * line["ms_per_step"] <= 1e3 * line["wall_s"]
 
 
 def test_batched_segment_reproduces_the_union_mesh_segment():
