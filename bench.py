@@ -86,6 +86,7 @@ def solver_options(args):
         kry.update(smoother=1, vanka_omega=0.86, nu_pre=args.nu, nu_post=args.nu)
     if args.coarse_jacobi:
         kry.update(coarse_smoother=0, nu_coarse=1)
+    kry.update(segment_krylov=int(args.segment_krylov))
     if args.nu_finest > 0 and args.smoother != "vanka":
         kry.update(nu_pre=args.nu_finest, nu_post=args.nu_finest)
     return dict(precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=int(args.graphs),
@@ -546,6 +547,8 @@ def main():
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "vanka"])
     ap.add_argument("--nu", type=int, default=1, help="Vanka sweeps before / after the coarse correction")
     ap.add_argument("--coarse-bf16", type=int, default=0, help="BF16 coarse-level operators in the V-cycle")
+    ap.add_argument("--segment-krylov", type=int, default=1,
+                    help="batched meshes: 1 = one Arnoldi process per segment, 0 = one over the union")
     ap.add_argument("--nu-finest", type=int, default=0,
                     help="block-Jacobi sweeps before / after on the finest level (0: the library default, 4)")
     ap.add_argument("--coarse-jacobi", action="store_true",
@@ -628,6 +631,9 @@ def main():
                                         else "minimal-residual block Jacobi 2+2"),
                        coarse_operators="BF16 (V-cycle reads)" if args.coarse_bf16 else "FP32",
                        aggregation=aggregation_of(args),
+                       krylov=("per-segment FGMRES (one Arnoldi process per segment)"
+                               if args.config == "batched" and args.segment_krylov and args.solver != "bicgstab-pl"
+                               else None),
                        krylov_its_per_step=round(res["krylov_per_step"], 1),
                        krylov_cap_hits_in_timed_steps=res["krylov_cap_hits"],
                        newton_cap_hits_in_timed_steps=res["newton_cap_hits"], amg_levels=res["levels"]),

@@ -170,6 +170,11 @@ typedef struct {
                                block-row kernels (4x4 level: CTA of 64, 128 or 256 threads;
                                7x7 levels: one CTA or one warp per block row) on this mesh
                                and keep the fastest (see fsi_solid_get_tuning); 0: defaults */
+  int32_t segment_krylov;   /* meshes of several segments (fsi_mesh_desc.seg_node), FGMRES:
+                               1 = one Arnoldi process per segment (per-segment inner
+                               products, Hessenberg matrices and stop, so each segment
+                               stops at its own convergence); 0 = one process over the
+                               union (the segments' right-hand sides scaled to unit norm) */
 } fsi_solver_opts;
 
 /* Load of one solve (device arrays owned by the caller; NULL = absent).

@@ -161,6 +161,12 @@ struct Handle {
   double* d_seg_a = nullptr;     // [n_seg] per-segment scratch
   double* d_seg_b = nullptr;
   double* h_seg = nullptr;       // pinned [n_seg]
+  // per-segment FGMRES (segment_krylov): [2 (m+2)][n_seg] dot products and
+  // [m+1][n_seg] coefficients, device and pinned host copies
+  double* d_sdots = nullptr;
+  double* h_sdots = nullptr;
+  double* d_scoef = nullptr;
+  double* h_scoef = nullptr;
   int* d_err = nullptr;          // device error word (bit 0 inverted, bit 1 bounds)
   // gather-based assembly: element buffers and fixed gather plans
   void* d_ebuf = nullptr;        // T [n_elems][16][16] element tangent blocks
@@ -301,6 +307,12 @@ void dn_diff(long m, const double* r, const double* r_prev, double* dr, cudaStre
 void segment_sumsq(const int32_t* seg_ptr, int n_seg, const double* x, double* out, cudaStream_t s);
 void segment_normalise(int n_seg, double* a, double* b, cudaStream_t s);
 void segment_scale(const int32_t* seg_node, const double* scale, double* x, long n, cudaStream_t s);
+// out_dev[i n_seg + s] = V_i . y over segment s (deterministic)
+void seg_dots(const int32_t* seg_ptr, int n_seg, const double* V, long ldv, int k, const double* y, double* out_dev,
+              cudaStream_t s);
+// w += sign * sum_i coef_dev[i n_seg + seg(t)] V_i[t]
+void seg_multi_axpy(const int32_t* seg_node, int n_seg, const double* coef_dev, const double* V, int k, long n,
+                    double* w, double sign, cudaStream_t s);
 
 }  // namespace fsi
 

@@ -866,6 +866,32 @@ __global__ void segment_sumsq_kernel(const int32_t* __restrict__ seg_ptr, const 
   if (threadIdx.x == 0) out[sg] = acc;
 }
 
+// Segmented reductions of the per-segment Krylov method: out[i n_seg + s] =
+// V_i . y over the unknowns of segment s (one CTA per (segment, vector), fixed
+// order: deterministic).
+__global__ void seg_multidot_kernel(const int32_t* __restrict__ seg_ptr, int n_seg, const double* __restrict__ V,
+                                    long ldv, const double* __restrict__ y, double* __restrict__ out) {
+  const int sg = blockIdx.x, i = blockIdx.y;
+  const long d0 = 4L * seg_ptr[sg], d1 = 4L * seg_ptr[sg + 1];
+  const double* v = V + (size_t)i * ldv;
+  double acc = 0.0;
+  for (long t = d0 + threadIdx.x; t < d1; t += blockDim.x) acc += v[t] * y[t];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[(size_t)i * n_seg + sg] = acc;
+}
+
+// w += sign * sum_i coef[i n_seg + seg(t)] V_i[t]
+__global__ void seg_multi_axpy_kernel(const int32_t* __restrict__ seg_node, int n_seg,
+                                      const double* __restrict__ coef, const double* __restrict__ V, int k, long n,
+                                      double sign, double* __restrict__ w) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const int sg = seg_node[t >> 2];
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += coef[(size_t)i * n_seg + sg] * V[(size_t)i * n + t];
+    w[t] += sign * acc;
+  }
+}
+
 // mode 0: a[s] = 1/sqrt(sumsq) (1 if zero), b[s] = sqrt(sumsq); x *= a[seg]  (normalise)
 __global__ void segment_normalise_kernel(int n_seg, double* __restrict__ a, double* __restrict__ b) {
   const int sg = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1375,6 +1401,20 @@ void to_double(const float* x, double* y, long n, cudaStream_t s) {
 
 void segment_sumsq(const int32_t* seg_ptr, int n_seg, const double* x, double* out, cudaStream_t s) {
   FSI_LAUNCH(fsi::KC_VECTOR, s, segment_sumsq_kernel<<<n_seg, kRedThreads, 0, s>>>(seg_ptr, x, out));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void seg_dots(const int32_t* seg_ptr, int n_seg, const double* V, long ldv, int k, const double* y, double* out_dev,
+              cudaStream_t s) {
+  dim3 grid(n_seg, k);
+  FSI_LAUNCH(fsi::KC_VECTOR, s, seg_multidot_kernel<<<grid, kRedThreads, 0, s>>>(seg_ptr, n_seg, V, ldv, y, out_dev));
+  FSI_CUDA_TRY(cudaGetLastError());
+}
+
+void seg_multi_axpy(const int32_t* seg_node, int n_seg, const double* coef_dev, const double* V, int k, long n,
+                    double* w, double sign, cudaStream_t s) {
+  FSI_LAUNCH(fsi::KC_VECTOR, s, seg_multi_axpy_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(seg_node, n_seg, coef_dev, V,
+                                                                                             k, n, sign, w));
   FSI_CUDA_TRY(cudaGetLastError());
 }
 

@@ -461,6 +461,146 @@ int fgmres(Handle& h, const double* b, double* x, double rtol, int maxit, double
   return total;
 }
 
+// FGMRES(m) with one Arnoldi process per segment of a batched mesh.  The
+// system is block diagonal by segment, so every inner product, norm,
+// Hessenberg column, Givens rotation and least-squares solve is taken per
+// segment: each segment converges at its own rate to rtol relative to its own
+// right-hand side, and a segment that has converged stops contributing (its
+// basis vectors and coefficients are zero from then on).  The preconditioner
+// (one V-cycle over the union hierarchy) acts on the union of the segments'
+// basis vectors; flexible GMRES asks nothing more of it.  Returns the
+// iterations of the slowest segment; *rel = the largest segment's
+// ||b_s - A x_s|| / ||b_s||.
+int fgmres_seg(Handle& h, const double* b, double* x, double rtol, int maxit, double* rel, cudaStream_t s) {
+  const long n = 4L * h.n_nodes;
+  const int m = h.m, ns = h.n_seg;
+  double* V = h.d_V;
+  double* Z = h.d_Z;
+  double* r = h.d_r;
+  auto seg_norms = [&](const double* v, std::vector<double>& out) {
+    segment_sumsq(h.d_seg_ptr, ns, v, h.d_seg_a, s);
+    FSI_CUDA_TRY(cudaMemcpyAsync(h.h_seg, h.d_seg_a, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    FSI_CUDA_TRY(cudaStreamSynchronize(s));
+    out.resize(ns);
+    for (int q = 0; q < ns; ++q) out[q] = std::sqrt(h.h_seg[q]);
+  };
+  auto set_scale = [&](const std::vector<double>& sc) {
+    for (int q = 0; q < ns; ++q) h.h_seg[q] = sc[q];
+    FSI_CUDA_TRY(cudaMemcpyAsync(h.d_seg_a, h.h_seg, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+  };
+  std::vector<double> bn, beta;
+  seg_norms(b, bn);
+  operator_residual(h, b, x, r, s);
+  seg_norms(r, beta);
+  std::vector<char> done(ns), live(ns);
+  auto converged = [&](int q) { return bn[q] == 0.0 || beta[q] <= rtol * bn[q]; };
+  for (int q = 0; q < ns; ++q) done[q] = converged(q);
+  const size_t hs = (size_t)(m + 1) * m;
+  std::vector<double> H(hs * ns), cs((size_t)m * ns), sn((size_t)m * ns), g((size_t)(m + 1) * ns), y(m),
+      sc(ns);
+  std::vector<int> jj(ns);
+  double* d_h1 = h.d_sdots;
+  double* d_h2 = h.d_sdots + (size_t)(m + 2) * ns;
+  int total = 0;
+  auto any_open = [&](const std::vector<char>& f, bool want) {
+    for (int q = 0; q < ns; ++q)
+      if ((bool)f[q] == want) return true;
+    return false;
+  };
+  while (any_open(done, false) && total < maxit) {
+    for (int q = 0; q < ns; ++q) {
+      live[q] = !done[q];
+      sc[q] = live[q] ? 1.0 / beta[q] : 0.0;
+      jj[q] = 0;
+      std::fill(g.begin() + (size_t)q * (m + 1), g.begin() + (size_t)(q + 1) * (m + 1), 0.0);
+      g[(size_t)q * (m + 1)] = live[q] ? beta[q] : 0.0;
+    }
+    FSI_CUDA_TRY(cudaMemcpyAsync(V, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    set_scale(sc);
+    segment_scale(h.d_seg_node, h.d_seg_a, V, n, s);
+    int jmax = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
+      precondition(h, vj, zj, s);
+      apply_operator(h, zj, w, s);
+      seg_dots(h.d_seg_ptr, ns, V, n, j + 2, w, d_h1, s);
+      seg_multi_axpy(h.d_seg_node, ns, d_h1, V, j + 1, n, w, -1.0, s);
+      seg_dots(h.d_seg_ptr, ns, V, n, j + 2, w, d_h2, s);
+      FSI_CUDA_TRY(cudaMemcpyAsync(h.h_sdots, h.d_sdots, sizeof(double) * (size_t)2 * (m + 2) * ns,
+                                   cudaMemcpyDeviceToHost, s));
+      FSI_CUDA_TRY(cudaStreamSynchronize(s));
+      seg_multi_axpy(h.d_seg_node, ns, d_h2, V, j + 1, n, w, -1.0, s);
+      const double* h1 = h.h_sdots;
+      const double* h2 = h.h_sdots + (size_t)(m + 2) * ns;
+      for (int q = 0; q < ns; ++q) {
+        sc[q] = 0.0;
+        if (!live[q]) continue;
+        double* Hq = &H[hs * q];
+        double* csq = &cs[(size_t)m * q];
+        double* snq = &sn[(size_t)m * q];
+        double* gq = &g[(size_t)(m + 1) * q];
+        double proj2 = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          Hq[(size_t)i * m + j] = h1[(size_t)i * ns + q] + h2[(size_t)i * ns + q];
+          proj2 += h2[(size_t)i * ns + q] * h2[(size_t)i * ns + q];
+        }
+        const double hn = std::sqrt(std::max(h2[(size_t)(j + 1) * ns + q] - proj2, 0.0));
+        Hq[(size_t)(j + 1) * m + j] = hn;
+        sc[q] = hn > 0.0 ? 1.0 / hn : 0.0;
+        for (int i = 0; i < j; ++i) {
+          const double a = Hq[(size_t)i * m + j], bb = Hq[(size_t)(i + 1) * m + j];
+          Hq[(size_t)i * m + j] = csq[i] * a + snq[i] * bb;
+          Hq[(size_t)(i + 1) * m + j] = -snq[i] * a + csq[i] * bb;
+        }
+        const double a = Hq[(size_t)j * m + j], bb = Hq[(size_t)(j + 1) * m + j];
+        const double d = std::hypot(a, bb);
+        csq[j] = d > 0 ? a / d : 1.0;
+        snq[j] = d > 0 ? bb / d : 0.0;
+        Hq[(size_t)j * m + j] = d;
+        Hq[(size_t)(j + 1) * m + j] = 0.0;
+        gq[j + 1] = -snq[j] * gq[j];
+        gq[j] = csq[j] * gq[j];
+        jj[q] = j + 1;
+        if (std::fabs(gq[j + 1]) <= rtol * bn[q] || hn == 0.0) {
+          live[q] = 0;   // converged in this cycle: no further basis vectors
+          sc[q] = 0.0;
+        }
+      }
+      set_scale(sc);
+      segment_scale(h.d_seg_node, h.d_seg_a, w, n, s);
+      ++total;
+      jmax = j + 1;
+      if (!any_open(live, true) || total >= maxit) break;
+    }
+    // per-segment least squares: y_q = R_q^-1 g_q over its first jj[q] columns
+    std::fill(h.h_scoef, h.h_scoef + (size_t)(m + 1) * ns, 0.0);
+    for (int q = 0; q < ns; ++q) {
+      const double* Hq = &H[hs * q];
+      const double* gq = &g[(size_t)(m + 1) * q];
+      const int k = jj[q];
+      for (int i = k - 1; i >= 0; --i) {
+        double acc = gq[i];
+        for (int c = i + 1; c < k; ++c) acc -= Hq[(size_t)i * m + c] * y[c];
+        y[i] = acc / Hq[(size_t)i * m + i];
+      }
+      for (int i = 0; i < k; ++i) h.h_scoef[(size_t)i * ns + q] = y[i];
+    }
+    FSI_CUDA_TRY(cudaMemcpyAsync(h.d_scoef, h.h_scoef, sizeof(double) * (size_t)jmax * ns, cudaMemcpyHostToDevice,
+                                 s));
+    if (jmax > 0) seg_multi_axpy(h.d_seg_node, ns, h.d_scoef, Z, jmax, n, x, 1.0, s);
+    operator_residual(h, b, x, r, s);
+    seg_norms(r, beta);
+    for (int q = 0; q < ns; ++q) done[q] = converged(q);
+  }
+  double worst = 0.0;
+  for (int q = 0; q < ns; ++q)
+    if (bn[q] > 0.0) worst = std::max(worst, beta[q] / bn[q]);
+  *rel = worst;
+  return total;
+}
+
 // BiCGStab (van der Vorst), right-preconditioned by the same V-cycle: the
 // paper's Krylov method for the solid (Sec. 5.4.2), here with the coupled AMG
 // preconditioner.  Short recurrences: no restart length, two preconditioner
@@ -532,6 +672,7 @@ void set_error(Handle* h, const std::string& msg) {
 
 int linear_solve(Handle& h, const double* b, double* x, double rtol, double* rel, cudaStream_t s) {
   if (h.opts.krylov == FSI_KRYLOV_BICGSTAB) return bicgstab(h, b, x, rtol, h.opts.max_krylov, rel, s);
+  if (h.n_seg > 1 && h.opts.segment_krylov) return fgmres_seg(h, b, x, rtol, h.opts.max_krylov, rel, s);
   return fgmres(h, b, x, rtol, h.opts.max_krylov, rel, s);
 }
 
@@ -795,6 +936,13 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
     h.d_dn_p = dalloc<double>(nn);
     FSI_CUDA_TRY(cudaStreamSynchronize(s));
   }
+  if (h.n_seg > 1) {
+    const size_t ns = (size_t)h.n_seg, mm = (size_t)h.m;
+    h.d_sdots = dalloc<double>(2 * (mm + 2) * ns);
+    h.d_scoef = dalloc<double>((mm + 1) * ns);
+    FSI_CUDA_TRY(cudaMallocHost((void**)&h.h_sdots, sizeof(double) * 2 * (mm + 2) * ns));
+    FSI_CUDA_TRY(cudaMallocHost((void**)&h.h_scoef, sizeof(double) * (mm + 1) * ns));
+  }
   h.red_blocks = 2 * 152;
   h.d_partial = dalloc<double>((size_t)h.red_blocks * (kMaxRestart + 1));
   h.d_dots = dalloc<double>(kDotSize);
@@ -844,6 +992,10 @@ static void destroy_impl(Handle* hp) {
     dfree(p);
   if (h.vc_exec) cudaGraphExecDestroy(h.vc_exec);
   if (h.h_dots) cudaFreeHost(h.h_dots);
+  if (h.h_sdots) cudaFreeHost(h.h_sdots);
+  if (h.h_scoef) cudaFreeHost(h.h_scoef);
+  dfree(h.d_sdots);
+  dfree(h.d_scoef);
   if (h.h_seg) cudaFreeHost(h.h_seg);
   dfree(h.d_seg_ptr);
   dfree(h.d_seg_a);
@@ -1099,6 +1251,7 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->nu_coarse = 2;
   o->coarse_smoother = FSI_COARSE_MR;
   o->autotune = 1;
+  o->segment_krylov = 1;
   o->coarse_max_nodes = 16;
   o->max_levels = 12;
   o->use_pspg = 1;
