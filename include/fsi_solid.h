@@ -169,7 +169,12 @@ typedef struct {
                                (CTA of 64 or 128 threads) and of every smoothed level's
                                block-row kernels (4x4 level: CTA of 64, 128 or 256 threads;
                                7x7 levels: one CTA or one warp per block row) on this mesh
-                               and keep the fastest (see fsi_solid_get_tuning); 0: defaults */
+                               and keep the fastest (see fsi_solid_get_tuning); 0: defaults.
+                               The choice rests on timings, so two handles can pick
+                               different shapes; the CTA- and warp-per-row kernels sum a
+                               block row in different orders, so their solutions agree to
+                               the Krylov tolerance, not bit for bit (autotune = 0 fixes
+                               the shapes; one handle is always bit-reproducible) */
   int32_t segment_krylov;   /* meshes of several segments (fsi_mesh_desc.seg_node), FGMRES:
                                1 = one Arnoldi process per segment (per-segment inner
                                products, Hessenberg matrices and stop, so each segment
