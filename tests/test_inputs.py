@@ -102,3 +102,44 @@ def test_batched_segment_reproduces_the_union_mesh_segment():
         assert np.allclose(m.fibre[em], t.fibre)
         assert np.allclose(m.face_pressure[m.seg_face == i], t.face_pressure)
         assert np.allclose(m.X[nodes, 1:], t.X[:, 1:]) and np.allclose(np.ptp(m.X[nodes, 0] - t.X[:, 0]), 0.0)
+
+
+def test_bench_ramp_driver_counts_newton_and_krylov_cap_hits():
+    """The bench's load ramp advances on a converged start residual or after 12
+    Newton steps (a Newton-cap hit), and counts linear solves that stopped at
+    the Krylov cap above their tolerance (host logic, scripted solver)."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class FakeTorch:
+        @staticmethod
+        def zeros(shape, device=None, dtype=None):
+            return types.SimpleNamespace(zero_=lambda: None)
+
+    class FakeSolver:
+        def __init__(self, script):
+            self.script = list(script)
+
+        def newton_step(self, state, load, check=False):
+            res0, kits, lin_res = self.script.pop(0)
+            return types.SimpleNamespace(status=0, res0=res0, krylov_its_last=kits, lin_res=lin_res)
+
+    # load 1: converges at the 3rd step; load 2: never converges -> 13 steps then advance
+    script = [(1.0, 10, 1e-9), (1e-3, 10, 1e-9), (1e-9, 600, 1e-6)]
+    script += [(1.0, 10, 1e-9)] + [(0.5, 10, 1e-9)] * 12
+    drv = bench.RampDriver.__new__(bench.RampDriver)
+    drv.Load = lambda **kw: kw
+    drv.fp = None
+    drv.solver = FakeSolver(script)
+    drv.torch = FakeTorch
+    drv.state = FakeTorch.zeros(())
+    drv.k, drv.r0, drv.newton_in_load = 1, None, 0
+    drv.max_krylov, drv.krylov_rtol = 600, 1e-8
+    drv.krylov_cap_hits = drv.newton_cap_hits = 0
+    for _ in range(3):
+        drv.step()
+    assert drv.k == 2 and drv.krylov_cap_hits == 1 and drv.newton_cap_hits == 0
+    for _ in range(13):
+        drv.step()
+    assert drv.k == 3 and drv.newton_cap_hits == 1
