@@ -38,6 +38,9 @@ def _compile(src: str, extra) -> str:
            "-I", INCLUDE, "-I", CSRC, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-v"] if os.environ.get("FSI_PTXAS_VERBOSE") else []
+    else:
+        # the host AMG set-up spreads its per-row value loops over the host's cores
+        cmd[1:1] = ["-Xcompiler", "-fopenmp"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
@@ -54,7 +57,7 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     out = lib_path()
     tmp = out + ".tmp"
     cmd = [nvcc_path(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+           "-Xlinker", "-rpath=/usr/local/cuda/lib64", "-lgomp"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{res.stdout}\n{res.stderr}")

@@ -9,7 +9,9 @@
 // w = 4 / (3 lambda_max(D^-1 A)), and the coarse operators are the Galerkin
 // products P^T A P.  What stays fixed per mesh is computed here: the
 // aggregates, P_t, w, and the sparsity patterns of P, A P and P^T A P
-// together with the index plans of those products.  Every Newton step then
+// together with the index plans of those products (the value loops run on
+// the host's cores with OpenMP, every row or block written by one thread, so
+// the result does not depend on the thread count).  Every Newton step then
 // recomputes on the device, with the current tangent, the smoothed P and the
 // Galerkin operators of all levels (a numeric-only set-up); keeping the
 // coarse operators of the reference state instead lets the Krylov iteration
@@ -243,6 +245,7 @@ double power_lambda(const HostBsr& A, const std::vector<double>& Dinv, const std
     nv = std::sqrt(nv);
     if (nv == 0.0) return 1.0;
     for (double& x : v) x /= nv;
+#pragma omp parallel for schedule(static) firstprivate(t)
     for (int i = 0; i < A.n; ++i) {
       std::fill(t.begin(), t.end(), 0.0);
       for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
@@ -280,14 +283,21 @@ void block_inverses(const HostBsr& A, std::vector<double>& Dinv) {
   const int b = A.br;
   Dinv.assign((size_t)A.n * b * b, 0.0);
   std::vector<double> blk(b * b);
+  int bad = 0;   // 1: a row without a diagonal block, 2: a singular diagonal block
+#pragma omp parallel for schedule(static) firstprivate(blk) reduction(| : bad)
   for (int i = 0; i < A.n; ++i) {
     int kd = -1;
     for (int k = A.rp[i]; k < A.rp[i + 1]; ++k)
       if (A.ci[k] == i) kd = k;
-    if (kd < 0) throw ArgError("AMG level without a diagonal block");
+    if (kd < 0) {
+      bad |= 1;
+      continue;
+    }
     for (int q = 0; q < b * b; ++q) blk[q] = A.v[(size_t)kd * b * b + q];
-    if (!invert_block(blk.data(), b, &Dinv[(size_t)i * b * b])) throw ArgError("singular diagonal block in AMG set-up");
+    if (!invert_block(blk.data(), b, &Dinv[(size_t)i * b * b])) bad |= 2;
   }
+  if (bad & 1) throw ArgError("AMG level without a diagonal block");
+  if (bad & 2) throw ArgError("singular diagonal block in AMG set-up");
 }
 
 }  // namespace
@@ -352,6 +362,7 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
     for (int i = 0; i <= n; ++i) Pt.rp[i] = i;
     for (int i = 0; i < n; ++i) Pt.ci[i] = agg[i];
     std::vector<double> Bc((size_t)nc * NS * NS, 0.0);
+#pragma omp parallel for schedule(dynamic, 64)
     for (int I = 0; I < nc; ++I) {
       const auto& mem = members[I];
       const int rows = b * (int)mem.size();
@@ -430,6 +441,7 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
     P.v.assign((size_t)P.nb() * pb, 0.0);
     {
       std::vector<double> W(pb), tmp(pb);
+#pragma omp parallel for schedule(dynamic, 256) firstprivate(W, tmp)
       for (int i = 0; i < n; ++i)
         for (int q = P.rp[i]; q < P.rp[i + 1]; ++q) {
           std::fill(W.begin(), W.end(), 0.0);
@@ -487,6 +499,7 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
         AP.rp[i + 1] = (int32_t)AP.ci.size();
       }
       AP.v.assign((size_t)AP.nb() * pb, 0.0);
+#pragma omp parallel for schedule(dynamic, 1024)
       for (int r = 0; r < AP.nb(); ++r)
         for (int s = ap_ptr[r]; s < ap_ptr[r + 1]; ++s)
           gemm_acc(&A.v[(size_t)ap_pairs[2 * s] * b * b], &P.v[(size_t)ap_pairs[2 * s + 1] * pb],
@@ -530,6 +543,7 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
         Ac.rp[I + 1] = (int32_t)Ac.ci.size();
       }
       Ac.v.assign((size_t)Ac.nb() * NS * NS, 0.0);
+#pragma omp parallel for schedule(dynamic, 1024)
       for (int B = 0; B < Ac.nb(); ++B)
         for (int s = ac_ptr[B]; s < ac_ptr[B + 1]; ++s)
           gemm_tn_acc(&P.v[(size_t)ac_pairs[2 * s] * pb], &AP.v[(size_t)ac_pairs[2 * s + 1] * pb],
