@@ -606,23 +606,9 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
     tot += (int64_t)nd * nd;
     coarse.max_dofs = std::max(coarse.max_dofs, nd);
   }
-  coarse.inv.assign((size_t)tot, 0.0);
-  return;   // the coarsest operator changes with K: it is factorised on the device per Newton step
-  for (int c = 0; c < ncomp_c; ++c) {
-    const int i0 = coarse.comp_ptr[c], i1 = coarse.comp_ptr[c + 1];
-    const int nd = b * (i1 - i0);
-    std::vector<double> M((size_t)nd * nd, 0.0);
-    for (int i = i0; i < i1; ++i)
-      for (int k = Lc.A.rp[i]; k < Lc.A.rp[i + 1]; ++k) {
-        const int j = Lc.A.ci[k];
-        if (j < i0 || j >= i1) continue;
-        for (int r = 0; r < b; ++r)
-          for (int q = 0; q < b; ++q)
-            M[(size_t)((i - i0) * b + r) * nd + (j - i0) * b + q] = Lc.A.v[((size_t)k * b + r) * b + q];
-      }
-    if (!invert_block(M.data(), nd, &coarse.inv[coarse.inv_off[c]]))
-      throw ArgError("singular coarsest AMG operator");
-  }
+  // the dense inverses themselves are formed on the device every Newton step,
+  // since the coarsest operator changes with K
+  coarse.inv_size = tot;
 }
 
 }  // namespace fsi

@@ -38,7 +38,7 @@ struct HostLevel {
 struct HostCoarse {
   std::vector<int32_t> comp_ptr;   // node ranges of the components of the coarsest level
   std::vector<int64_t> inv_off;    // offsets of the dense inverses
-  std::vector<double> inv;         // dense inverses (unused when the device factorises)
+  int64_t inv_size = 0;            // entries of all dense inverses together
   int max_dofs = 0;
 };
 

@@ -126,7 +126,6 @@ struct Level {
 struct Coarse {              // block-diagonal dense inverse of the coarsest level
   int n_comp = 0;
   int max_dofs = 0;
-  bool on_device_factor = false;  // single-level hierarchies factorise K itself each Newton step
   int32_t* comp_ptr = nullptr;   // [n_comp+1] node ranges (components are contiguous)
   int64_t* inv_off = nullptr;    // [n_comp] offsets into inv (in entries)
   void* inv = nullptr;           // T dense inverses, row-major per component

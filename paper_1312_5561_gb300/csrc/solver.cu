@@ -265,9 +265,8 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
   C.max_dofs = hc.max_dofs;
   C.comp_ptr = upload(hc.comp_ptr, s);
   C.inv_off = upload(hc.inv_off, s);
-  C.on_device_factor = true;
-  C.inv = dalloc<char>(ts * hc.inv.size());
-  C.work = dalloc<double>(hc.inv.size());
+  C.inv = dalloc<char>(ts * (size_t)hc.inv_size);
+  C.work = dalloc<double>((size_t)hc.inv_size);
   FSI_CUDA_TRY(cudaStreamSynchronize(s));
 }
 

@@ -1,0 +1,148 @@
+"""The host smoothed-aggregation set-up (aggregates, tentative prolongator,
+prolongator smoothing and Galerkin products of the reference tangent), run on
+the CPU through a small C++ driver on the oracle tangent of a two-layer tube.
+
+Checked here, without a GPU: the hierarchy is bitwise the same at any OpenMP
+thread count, and levels 0 and 1 satisfy the definitions of smoothed
+aggregation (Sec. 5.5: Galerkin coarse levels) recomputed with scipy."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.csgraph  # noqa: F401  (sp.csgraph)
+
+import oracle.solid as O
+from fixtures import artery_layers, artery_tube
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1312_5561_gb300", "csrc")
+NS = 7
+
+
+def _cuda_include():
+    for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            return os.path.join(d, "include")
+    return None
+
+
+@pytest.fixture(scope="module")
+def exe(tmp_path_factory):
+    inc = _cuda_include()
+    if shutil.which("g++") is None or inc is None:
+        pytest.skip("needs g++ and the CUDA runtime headers")
+    out = str(tmp_path_factory.mktemp("amg") / "host_amg_setup_main")
+    subprocess.run(["g++", "-O2", "-fopenmp", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-I", inc,
+                    os.path.join(ROOT, "tests", "host_amg_setup_main.cpp"), os.path.join(CSRC, "amg_setup.cpp"), "-o",
+                    out], check=True, capture_output=True, text=True)
+    return out
+
+
+@pytest.fixture(scope="module")
+def problem(tmp_path_factory):
+    """Oracle tangent of a 32 x 8 x 8 tube (12,288 tets, 2,592 nodes) at a
+    pressurised state, as 4 x 4 blocks with identity Dirichlet rows."""
+    mesh = artery_tube(n_theta=32, n_z=8, length=0.5, materials=artery_layers(1.0e3))
+    P = O.Problem(mesh)
+    rng = np.random.default_rng(11)
+    state = 0.002 * rng.standard_normal((mesh.n_nodes, 4)) * P.free
+    K = P.tangent(state).tobsr(blocksize=(4, 4))
+    K.sort_indices()
+    d = str(tmp_path_factory.mktemp("amg_in"))
+    n = mesh.n_nodes
+    np.array([n, K.indices.size], dtype=np.int64).tofile(os.path.join(d, "dims.bin"))
+    K.indptr.astype(np.int32).tofile(os.path.join(d, "rp.bin"))
+    K.indices.astype(np.int32).tofile(os.path.join(d, "ci.bin"))
+    K.data.astype(np.float64).tofile(os.path.join(d, "v.bin"))
+    free = P.free.astype(np.uint8)
+    free.tofile(os.path.join(d, "free.bin"))
+    np.ascontiguousarray(mesh.X, dtype=np.float64).tofile(os.path.join(d, "X.bin"))
+    return dict(dir=d, n=n, K=K.tocsr(), free=free.ravel(), X=mesh.X)
+
+
+def _run(exe, d, mode, threads):
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    out = subprocess.run([exe, d, mode], capture_output=True, text=True, env=env, timeout=300)
+    assert out.returncode == 0, out.stderr
+    nlev, n1, h = out.stdout.split()
+    return int(nlev), int(n1), h
+
+
+def _read(d, name, dtype):
+    return np.fromfile(os.path.join(d, name), dtype=dtype)
+
+
+def _bsr(d, pre, n, nc, br, bc):
+    rp = _read(d, pre + "_rp.bin", np.int32)
+    ci = _read(d, pre + "_ci.bin", np.int32)
+    v = _read(d, pre + "_v.bin", np.float64).reshape(-1, br, bc)
+    assert rp.size == n + 1 and ci.size == v.shape[0] == rp[-1]
+    return sp.bsr_matrix((v, ci, rp), shape=(n * br, nc * bc)).tocsr()
+
+
+@pytest.mark.parametrize("mode", ["ring", "grow"])
+def test_hierarchy_is_the_same_at_any_thread_count(exe, problem, mode):
+    runs = [_run(exe, problem["dir"], mode, t) for t in (1, 2, 5)]
+    assert runs[0][0] >= 2
+    assert runs[1] == runs[0] and runs[2] == runs[0]
+
+
+@pytest.mark.parametrize("mode", ["ring", "grow"])
+def test_levels_0_and_1_follow_the_smoothed_aggregation_definitions(exe, problem, mode):
+    d, n = problem["dir"], problem["n"]
+    _, nc, _ = _run(exe, d, mode, 3)
+    A0 = problem["K"]
+    free0 = problem["free"].astype(np.float64)
+    F = sp.diags(free0)
+    # diagonal block inverses
+    Dinv = _read(d, "l0_Dinv.bin", np.float64).reshape(n, 4, 4)
+    Dblk = np.stack([A0[4 * i:4 * i + 4, 4 * i:4 * i + 4].toarray() for i in range(n)])
+    assert np.abs(np.einsum("nij,njk->nik", Dblk, Dinv) - np.eye(4)).max() <= 1e-10
+    # aggregates: every node in one aggregate, every aggregate used and connected
+    # in the block graph of A (roots take up to 7 neighbours, leftover nodes join
+    # a neighbouring aggregate), about 8 nodes per aggregate
+    agg = _read(d, "l0_agg.bin", np.int32)
+    assert agg.size == n and agg.min() == 0 and agg.max() == nc - 1
+    assert np.bincount(agg, minlength=nc).min() >= 1 and 4.0 <= n / nc <= 9.0
+    Gb = sp.csr_matrix((np.ones(A0.nnz), A0.indices // 4, A0.indptr[::4]), shape=(n, n)).tocoo()
+    keep = agg[Gb.row] == agg[Gb.col]
+    inner = sp.csr_matrix((np.ones(keep.sum()), (Gb.row[keep], Gb.col[keep])), shape=(n, n))
+    assert sp.csgraph.connected_components(inner, directed=False)[0] == nc
+    # tentative prolongator: one 4 x 7 block per node in its aggregate's column,
+    # orthonormal columns per aggregate (dependent ones dropped), and the rigid
+    # body modes + constant pressure on the free rows lie in its range
+    Ptv = _read(d, "l0_Pt.bin", np.float64).reshape(n, 4, NS)
+    rows = (4 * np.arange(n)[:, None, None] + np.arange(4)[None, :, None]).repeat(NS, 2)
+    cols = (NS * agg[:, None, None] + np.arange(NS)[None, None, :]).repeat(4, 1)
+    Pt = sp.csr_matrix((Ptv.ravel(), (rows.ravel(), cols.ravel())), shape=(4 * n, NS * nc))
+    G = (Pt.T @ Pt).toarray()
+    g = np.diag(G)
+    assert np.all((np.abs(g - 1.0) <= 1e-12) | (np.abs(g) <= 1e-12))
+    assert np.abs(G - np.diag(g)).max() <= 1e-12
+    X = problem["X"] - problem["X"].mean(axis=0)
+    B = np.zeros((n, 4, NS))
+    B[:, 0, 0] = B[:, 1, 1] = B[:, 2, 2] = B[:, 3, 6] = 1.0
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    B[:, 1, 3], B[:, 2, 3] = -z, y          # rotation about x: e_x x r
+    B[:, 0, 4], B[:, 2, 4] = z, -x          # about y
+    B[:, 0, 5], B[:, 1, 5] = -y, x          # about z
+    FB = F @ B.reshape(4 * n, NS)
+    assert np.abs(FB - Pt @ (Pt.T @ FB)).max() <= 1e-10 * np.abs(FB).max()
+    # smoothed prolongator P = F (I - omega D^-1 A) Pt
+    omega = _read(d, "l0_omega.bin", np.float64)[0]
+    assert 0.0 < omega < 10.0
+    Dm = sp.block_diag(list(Dinv), format="csr")
+    P = _bsr(d, "l0_P", n, nc, 4, NS)
+    Pref = F @ (Pt - omega * (Dm @ (A0 @ Pt)))
+    assert abs(P - Pref).max() <= 1e-12 * abs(Pref).max()
+    # Galerkin coarse operator A1 = P^T A0 P, identity rows for unknowns with no fine support
+    A1 = _bsr(d, "l1_A", nc, nc, NS, NS)
+    free1 = _read(d, "l1_free.bin", np.uint8).astype(np.float64)
+    assert free1.size == NS * nc
+    empty = np.asarray(abs(P).sum(axis=0)).ravel() == 0.0
+    assert np.array_equal(free1 == 0.0, empty)
+    Aref = (P.T @ A0 @ P) + sp.diags(1.0 - free1)
+    assert abs(A1 - Aref).max() <= 1e-12 * abs(Aref).max()
