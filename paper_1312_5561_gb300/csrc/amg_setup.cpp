@@ -186,47 +186,67 @@ HostBsr transpose(const HostBsr& P) {
   return T;
 }
 
-// C = A * B for block matrices (A: br x bk blocks, B: bk x bc blocks).
-HostBsr spgemm(const HostBsr& A, const HostBsr& B) {
-  HostBsr C;
-  C.n = A.n;
-  C.nc = B.nc;
-  C.br = A.br;
-  C.bc = B.bc;
-  const int ab = A.br * A.bc, bbz = B.br * B.bc, cb = C.br * C.bc;
-  C.rp.assign(C.n + 1, 0);
-  std::vector<int32_t> marker(B.nc, -1);
-  std::vector<int32_t> cols;
-  std::vector<double> acc;
-  for (int i = 0; i < A.n; ++i) {
-    cols.clear();
-    for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-      const int j = A.ci[k];
-      for (int q = B.rp[j]; q < B.rp[j + 1]; ++q) {
-        const int J = B.ci[q];
-        if (marker[J] < 0) {
-          marker[J] = (int)cols.size();
-          cols.push_back(J);
+// Pattern and pair plan of a sparse product built row by row: enum_row(i,
+// emit) calls emit(column, x, y) for every pair (x, y) that contributes to
+// output row i, in a fixed order.  The pairs are grouped by output column
+// (ascending), each group keeping that order, so that a later sum over a
+// group adds its products in the same order every time.  force_diag adds the
+// diagonal column to every row, with no pairs if none reach it.  Rows are
+// processed in contiguous chunks on the host's cores and the chunks are
+// concatenated in row order: the result does not depend on the thread count.
+template <typename EnumRow>
+void pair_plan(int n_rows, bool force_diag, const EnumRow& enum_row, std::vector<int32_t>& rp,
+               std::vector<int32_t>& ci, std::vector<int32_t>& ptr, std::vector<int32_t>& pairs) {
+  struct Chunk {
+    std::vector<int32_t> row_len, ci, grp_len, pairs;
+  };
+  constexpr int kRows = 512;
+  const int n_chunks = (n_rows + kRows - 1) / kRows;
+  std::vector<Chunk> chunks(n_chunks);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int c = 0; c < n_chunks; ++c) {
+    Chunk& ch = chunks[c];
+    struct Trip {
+      int32_t col, x, y;
+    };
+    std::vector<Trip> trip;
+    for (int i = c * kRows; i < std::min(n_rows, (c + 1) * kRows); ++i) {
+      trip.clear();
+      enum_row(i, [&](int32_t col, int32_t x, int32_t y) { trip.push_back({col, x, y}); });
+      std::stable_sort(trip.begin(), trip.end(), [](const Trip& a, const Trip& b) { return a.col < b.col; });
+      bool diag_open = force_diag;
+      int len = 0;
+      auto open_group = [&](int32_t col) {
+        ch.ci.push_back(col);
+        ch.grp_len.push_back(0);
+        ++len;
+      };
+      for (size_t t = 0; t < trip.size(); ++t) {
+        if (t == 0 || trip[t].col != trip[t - 1].col) {
+          if (diag_open && trip[t].col >= i) {
+            if (trip[t].col > i) open_group(i);
+            diag_open = false;
+          }
+          open_group(trip[t].col);
         }
+        ch.grp_len.back()++;
+        ch.pairs.push_back(trip[t].x);
+        ch.pairs.push_back(trip[t].y);
       }
+      if (diag_open) open_group(i);
+      ch.row_len.push_back(len);
     }
-    std::vector<int32_t> sorted = cols;
-    std::sort(sorted.begin(), sorted.end());
-    for (size_t q = 0; q < sorted.size(); ++q) marker[sorted[q]] = (int)q;
-    acc.assign(sorted.size() * cb, 0.0);
-    for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-      const int j = A.ci[k];
-      for (int q = B.rp[j]; q < B.rp[j + 1]; ++q) {
-        const int J = B.ci[q];
-        gemm_acc(&A.v[(size_t)k * ab], &B.v[(size_t)q * bbz], &acc[(size_t)marker[J] * cb], A.br, A.bc, B.bc);
-      }
-    }
-    C.ci.insert(C.ci.end(), sorted.begin(), sorted.end());
-    C.v.insert(C.v.end(), acc.begin(), acc.end());
-    C.rp[i + 1] = (int32_t)C.ci.size();
-    for (int J : sorted) marker[J] = -1;
   }
-  return C;
+  rp.assign(1, 0);
+  ci.clear();
+  ptr.assign(1, 0);
+  pairs.clear();
+  for (const Chunk& ch : chunks) {
+    for (int l : ch.row_len) rp.push_back(rp.back() + l);
+    ci.insert(ci.end(), ch.ci.begin(), ch.ci.end());
+    for (int l : ch.grp_len) ptr.push_back(ptr.back() + l);
+    pairs.insert(pairs.end(), ch.pairs.begin(), ch.pairs.end());
+  }
 }
 
 double power_lambda(const HostBsr& A, const std::vector<double>& Dinv, const std::vector<uint8_t>& freem) {
@@ -471,33 +491,12 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
     AP.nc = nc;
     AP.br = b;
     AP.bc = NS;
-    AP.rp.assign(n + 1, 0);
-    std::vector<int32_t> ap_ptr{0}, ap_pairs;
+    std::vector<int32_t> ap_ptr, ap_pairs;
     {
-      std::vector<int32_t> marker(nc, -1), cols;
-      std::vector<std::vector<int32_t>> lists;
-      for (int i = 0; i < n; ++i) {
-        cols.clear();
+      pair_plan(n, false, [&](int i, auto&& emit) {
         for (int k = A.rp[i]; k < A.rp[i + 1]; ++k)
-          for (int q = P.rp[A.ci[k]]; q < P.rp[A.ci[k] + 1]; ++q)
-            if (marker[P.ci[q]] < 0) { marker[P.ci[q]] = 0; cols.push_back(P.ci[q]); }
-        std::sort(cols.begin(), cols.end());
-        for (size_t t = 0; t < cols.size(); ++t) marker[cols[t]] = (int)t;
-        lists.assign(cols.size(), {});
-        for (int k = A.rp[i]; k < A.rp[i + 1]; ++k)
-          for (int q = P.rp[A.ci[k]]; q < P.rp[A.ci[k] + 1]; ++q) {
-            auto& lst = lists[marker[P.ci[q]]];
-            lst.push_back(k);
-            lst.push_back(q);
-          }
-        for (size_t t = 0; t < cols.size(); ++t) {
-          AP.ci.push_back(cols[t]);
-          ap_pairs.insert(ap_pairs.end(), lists[t].begin(), lists[t].end());
-          ap_ptr.push_back((int32_t)(ap_pairs.size() / 2));
-          marker[cols[t]] = -1;
-        }
-        AP.rp[i + 1] = (int32_t)AP.ci.size();
-      }
+          for (int q = P.rp[A.ci[k]]; q < P.rp[A.ci[k] + 1]; ++q) emit(P.ci[q], k, q);
+      }, AP.rp, AP.ci, ap_ptr, ap_pairs);
       AP.v.assign((size_t)AP.nb() * pb, 0.0);
 #pragma omp parallel for schedule(dynamic, 1024)
       for (int r = 0; r < AP.nb(); ++r)
@@ -509,39 +508,14 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
     HostBsr Ac;
     Ac.n = Ac.nc = nc;
     Ac.br = Ac.bc = NS;
-    Ac.rp.assign(nc + 1, 0);
-    std::vector<int32_t> ac_ptr{0}, ac_pairs;
+    std::vector<int32_t> ac_ptr, ac_pairs;
     {
-      std::vector<int32_t> marker(nc, -1), cols;
-      std::vector<std::vector<int32_t>> lists;
-      for (int I = 0; I < nc; ++I) {
-        cols.clear();
+      pair_plan(nc, true, [&](int I, auto&& emit) {
         for (int t = PT.rp[I]; t < PT.rp[I + 1]; ++t) {
           const int i = PT.ci[t];
-          for (int r = AP.rp[i]; r < AP.rp[i + 1]; ++r)
-            if (marker[AP.ci[r]] < 0) { marker[AP.ci[r]] = 0; cols.push_back(AP.ci[r]); }
+          for (int r = AP.rp[i]; r < AP.rp[i + 1]; ++r) emit(AP.ci[r], pt_src[t], r);
         }
-        if (std::find(cols.begin(), cols.end(), I) == cols.end()) cols.push_back(I);
-        std::sort(cols.begin(), cols.end());
-        for (size_t t = 0; t < cols.size(); ++t) marker[cols[t]] = (int)t;
-        lists.assign(cols.size(), {});
-        for (int t = PT.rp[I]; t < PT.rp[I + 1]; ++t) {
-          const int i = PT.ci[t];
-          const int q = pt_src[t];
-          for (int r = AP.rp[i]; r < AP.rp[i + 1]; ++r) {
-            auto& lst = lists[marker[AP.ci[r]]];
-            lst.push_back(q);
-            lst.push_back(r);
-          }
-        }
-        for (size_t t = 0; t < cols.size(); ++t) {
-          Ac.ci.push_back(cols[t]);
-          ac_pairs.insert(ac_pairs.end(), lists[t].begin(), lists[t].end());
-          ac_ptr.push_back((int32_t)(ac_pairs.size() / 2));
-          marker[cols[t]] = -1;
-        }
-        Ac.rp[I + 1] = (int32_t)Ac.ci.size();
-      }
+      }, Ac.rp, Ac.ci, ac_ptr, ac_pairs);
       Ac.v.assign((size_t)Ac.nb() * NS * NS, 0.0);
 #pragma omp parallel for schedule(dynamic, 1024)
       for (int B = 0; B < Ac.nb(); ++B)
