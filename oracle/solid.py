@@ -31,7 +31,7 @@ Every array here is float64 (or complex128 inside the complex step).
 from __future__ import annotations
 
 import dataclasses
-from typing import Optional, Sequence
+from typing import Optional
 
 import numpy as np
 import scipy.sparse as sp

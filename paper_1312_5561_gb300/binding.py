@@ -277,9 +277,10 @@ class SolidSolver:
         col_idx = np.empty(nb.value, np.int32)
         vals = np.empty((nb.value, 4, 4), np.float32 if dt.value == 1 else np.float64)
         cudart = _cudart()
-        cudart.cudaMemcpy(row_ptr.ctypes.data, rp, row_ptr.nbytes, 2)
-        cudart.cudaMemcpy(col_idx.ctypes.data, ci, col_idx.nbytes, 2)
-        cudart.cudaMemcpy(vals.ctypes.data, vv, vals.nbytes, 2)
+        for host, dev in ((row_ptr, rp), (col_idx, ci), (vals, vv)):
+            err = cudart.cudaMemcpy(host.ctypes.data, dev, host.nbytes, 2)   # 2: device to host
+            if err != 0:
+                raise FsiError(-2, f"cudaMemcpy of the assembled matrix failed with CUDA error {err}")
         return row_ptr, col_idx, vals
 
     def spmv(self, x, y=None):
@@ -443,7 +444,6 @@ _CUDART = None
 def _cudart():
     global _CUDART
     if _CUDART is None:
-        import ctypes.util
         for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so.13"):
             try:
                 _CUDART = C.CDLL(name)

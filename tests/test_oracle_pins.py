@@ -11,7 +11,7 @@ import scipy.optimize as so
 from scipy.linalg import expm
 
 from fixtures import (Material, artery_tube, cube_uniaxial_bc, kuhn_cube, mooney_rivlin)
-from fixtures.meshes import MODEL_ARTERY, MODEL_MOONEY_RIVLIN
+from fixtures.meshes import MODEL_ARTERY
 from oracle import solid as O
 
 
