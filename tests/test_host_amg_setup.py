@@ -6,7 +6,6 @@ Checked here, without a GPU: the hierarchy is bitwise the same at any OpenMP
 thread count, and levels 0 and 1 satisfy the definitions of smoothed
 aggregation (Sec. 5.5: Galerkin coarse levels) recomputed with scipy."""
 import os
-import shutil
 import subprocess
 
 import numpy as np
@@ -16,29 +15,15 @@ import scipy.sparse.csgraph  # noqa: F401  (sp.csgraph)
 
 import oracle.solid as O
 from fixtures import artery_layers, artery_tube
+from host_cxx import compile_driver
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_1312_5561_gb300", "csrc")
 NS = 7
-
-
-def _cuda_include():
-    for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"):
-        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
-            return os.path.join(d, "include")
-    return None
 
 
 @pytest.fixture(scope="module")
 def exe(tmp_path_factory):
-    inc = _cuda_include()
-    if shutil.which("g++") is None or inc is None:
-        pytest.skip("needs g++ and the CUDA runtime headers")
-    out = str(tmp_path_factory.mktemp("amg") / "host_amg_setup_main")
-    subprocess.run(["g++", "-O2", "-fopenmp", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-I", inc,
-                    os.path.join(ROOT, "tests", "host_amg_setup_main.cpp"), os.path.join(CSRC, "amg_setup.cpp"), "-o",
-                    out], check=True, capture_output=True, text=True)
-    return out
+    return compile_driver("host_amg_setup_main.cpp", ["amg_setup.cpp"],
+                          tmp_path_factory.mktemp("amg") / "host_amg_setup_main")
 
 
 @pytest.fixture(scope="module")
