@@ -54,7 +54,11 @@ enum { FSI_MODEL_MOONEY_RIVLIN = 0, FSI_MODEL_ARTERY = 1 };
  *  dir_mask  [n_nodes][4]  1 = Dirichlet-constrained component (Eq. elasbnd)
  *  neu_faces [n_faces][3]  boundary triangles carrying the dead pressure load;
  *                          the right-hand normal (x1-x0)x(x2-x0) points out
- *  seg_node  [n_nodes]     segment id (batched independent meshes) or NULL */
+ *  seg_node  [n_nodes]     segment id (batched independent meshes) or NULL:
+ *                          ids in [0, n_segments), non-decreasing in the node
+ *                          index, and the four vertices of every element in one
+ *                          segment; otherwise create returns FSI_ERR_ARG
+ *  n_segments              number of segments (read only with seg_node) */
 typedef struct {
   int32_t n_nodes;
   int32_t n_elems;

@@ -708,6 +708,19 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
       int v = mesh->neu_faces[3 * f + a];
       if (v < 0 || v >= nn) throw ArgError("face vertex out of range");
     }
+  if (mesh->seg_node) {
+    // segments are independent meshes: contiguous node ranges, every element inside one
+    const int32_t* sg = mesh->seg_node;
+    if (mesh->n_segments < 1) throw ArgError("seg_node given but n_segments < 1");
+    for (int i = 0; i < nn; ++i) {
+      if (sg[i] < 0 || sg[i] >= mesh->n_segments) throw ArgError("seg_node out of range at node " + std::to_string(i));
+      if (i > 0 && sg[i] < sg[i - 1]) throw ArgError("seg_node must be non-decreasing (segments contiguous)");
+    }
+    for (int e = 0; e < ne; ++e)
+      for (int a = 1; a < 4; ++a)
+        if (sg[mesh->tets[4 * e + a]] != sg[mesh->tets[4 * e]])
+          throw ArgError("element " + std::to_string(e) + " joins two segments");
+  }
 
   Handle* hp = new Handle();
   // a create that fails part-way releases what it has allocated
@@ -791,8 +804,6 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
   std::vector<int32_t> comp(nn, 0);
   if (mesh->seg_node)
     for (int i = 0; i < nn; ++i) comp[i] = mesh->seg_node[i];
-  for (int i = 1; i < nn; ++i)
-    if (comp[i] < comp[i - 1]) throw ArgError("seg_node must be non-decreasing (segments contiguous)");
   h.n_seg = nn ? comp[nn - 1] + 1 : 1;
   h.seg_ptr_host.assign(h.n_seg + 1, 0);
   for (int i = 0; i < nn; ++i) h.seg_ptr_host[comp[i] + 1]++;

@@ -64,3 +64,38 @@ def test_create_error_is_reported_without_gpu_work(lib):
     st = b.lib.fsi_solid_create(None, 0, None, None, ctypes.byref(h))
     assert st == -1 and not h.value
     assert b"required" in b.lib.fsi_solid_last_error(None)
+
+
+def _one_tet_desc(seg, n_segments):
+    """A single positively oriented tetrahedron with the given segment ids."""
+    import numpy as np
+    from paper_1312_5561_gb300 import binding as b
+    keep = dict(X=np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float64),
+                tets=np.array([[0, 1, 2, 3]], np.int32), mat=np.zeros(1, np.int32),
+                mask=np.zeros((4, 4), np.uint8), seg=np.asarray(seg, np.int32))
+    d = b.MeshDesc()
+    d.n_nodes, d.n_elems = 4, 1
+    d.X, d.tets, d.mat_id = keep["X"].ctypes.data, keep["tets"].ctypes.data, keep["mat"].ctypes.data
+    d.dir_mask = keep["mask"].ctypes.data
+    d.n_segments = n_segments
+    d.seg_node = keep["seg"].ctypes.data
+    mats = (b.MaterialDesc * 1)(b.MaterialDesc(0, 0.5, 0.1, 0.0, 1.0, 500.0, 0.0))
+    return d, mats, keep
+
+
+@pytest.mark.parametrize("seg, n_segments, msg", [
+    ([0, 0, 1, 1], 2, b"joins two segments"),
+    ([-1, 0, 0, 0], 1, b"seg_node out of range"),
+    ([0, 0, 0, 2], 2, b"seg_node out of range"),
+    ([1, 1, 0, 0], 2, b"non-decreasing"),
+    ([0, 0, 0, 0], 0, b"n_segments < 1"),
+])
+def test_bad_segment_tables_are_rejected_before_gpu_work(lib, seg, n_segments, msg):
+    """Segment ids outside [0, n_segments), a decreasing table or an element
+    spanning two segments is an argument error found on the host."""
+    from paper_1312_5561_gb300 import binding as b
+    d, mats, keep = _one_tet_desc(seg, n_segments)
+    h = ctypes.c_void_p()
+    st = b.lib.fsi_solid_create(ctypes.byref(d), 1, mats, None, ctypes.byref(h))
+    assert st == -1 and not h.value
+    assert msg in b.lib.fsi_solid_last_error(None)
