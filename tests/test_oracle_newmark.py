@@ -99,3 +99,77 @@ def test_inertia_of_a_rigid_translation():
     Pfree = O.Problem(dataclasses.replace(mesh, dir_mask=np.zeros_like(mesh.dir_mask)), O.Options(inertia_coef=c))
     tot = Pfree.residual(s, hist=np.zeros((mesh.n_nodes, 3)))[:, :3].sum(axis=0)
     assert np.allclose(tot, 1.2 * c * Pfree.V.sum() * t, rtol=1e-12, atol=0)
+
+
+def _deformed_state(mesh, seed):
+    """A smooth deformation with a pressure field (no inverted element)."""
+    rng = np.random.default_rng(seed)
+    X = mesh.X
+    s = np.zeros((mesh.n_nodes, 4))
+    s[:, :3] = 0.01 * np.sin(X @ rng.standard_normal((3, 3)))
+    s[:, 3] = 0.05 * np.cos(X @ rng.standard_normal(3))
+    return s * (mesh.dir_mask == 0)
+
+
+def test_zero_density_is_the_quasi_static_problem():
+    """rho -> 0: with rho = 0 the inertia coefficient and any history change
+    neither the residual nor the tangent (also not through the PSPG term)."""
+    mesh = artery_tube(n_theta=16, n_z=2, length=0.125, materials=artery_layers(1.0e3, rho=0.0))
+    s = _deformed_state(mesh, 1)
+    hist = np.random.default_rng(2).standard_normal((mesh.n_nodes, 3))
+    c = 1.0 / (0.625 * 0.01 ** 2)
+    Pq = O.Problem(mesh)
+    Pd = O.Problem(mesh, O.Options(inertia_coef=c))
+    assert np.array_equal(Pd.residual(s, hist=hist), Pq.residual(s))
+    Kd, Kq = Pd.tangent(s, hist=hist), Pq.tangent(s)
+    assert abs(Kd - Kq).max() <= 1e-14 * abs(Kq).max()
+
+
+def test_history_of_a_motion_without_acceleration_leaves_the_static_residual():
+    """With h = c d (c = 1/(beta dt^2)) the Newmark acceleration vanishes at every
+    node, so for any deformation d and pressure p the dynamic residual equals the
+    quasi-static one; the inertia term alone is of size rho c V |d|."""
+    mesh = artery_tube(n_theta=16, n_z=2, length=0.125, materials=artery_layers(1.0e3, rho=1.2))
+    s = _deformed_state(mesh, 3)
+    c = 1.0 / (0.625 * 0.01 ** 2)
+    Pq = O.Problem(mesh)
+    Pd = O.Problem(mesh, O.Options(inertia_coef=c))
+    Rq = Pq.residual(s)
+    Rd = Pd.residual(s, hist=c * s[:, :3])
+    scale = 1.2 * c * Pd.V.max() * np.abs(s[:, :3]).max()
+    assert np.abs(Rd - Rq).max() <= 1e-12 * scale
+    # and a history off by a uniform acceleration a gives the consistent inertial force rho V a in total
+    a = np.array([0.3, -0.1, 0.2])
+    Pfree = O.Problem(dataclasses.replace(mesh, dir_mask=np.zeros_like(mesh.dir_mask)), O.Options(inertia_coef=c))
+    Pfq = O.Problem(dataclasses.replace(mesh, dir_mask=np.zeros_like(mesh.dir_mask)))
+    s_free = _deformed_state(dataclasses.replace(mesh, dir_mask=np.zeros_like(mesh.dir_mask)), 3)
+    tot = (Pfree.residual(s_free, hist=c * s_free[:, :3] - a) - Pfq.residual(s_free))[:, :3].sum(axis=0)
+    assert np.allclose(tot, 1.2 * Pfree.V.sum() * a, rtol=1e-10, atol=0)
+
+
+def test_inertia_of_one_accelerated_vertex_on_a_single_tetrahedron():
+    """One unit right tetrahedron at rest (F = I, p = 0), acceleration a at
+    vertex 0 only (history h_0 = -a, h = 0 elsewhere, d = 0): the consistent P1
+    mass gives the forces rho V a (1 + delta_a0)/20, i.e. rho V a/10 at vertex 0
+    and rho V a/20 at the others (a lumped mass would give rho V a/4 and 0), and
+    the PSPG term gives tau V (rho hbar) . g_a = -tau V rho (a . g_a)/4 on the
+    pressure rows, with tau = h_T^2/(4 mu_l), h_T = sqrt 2, mu_l = 2 (c10 + c01)."""
+    from fixtures import mooney_rivlin
+    from fixtures.meshes import Mesh
+    c10, c01, rho = 0.5, 0.1, 1.2
+    mesh = Mesh(X=np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float64),
+                tets=np.array([[0, 1, 2, 3]], np.int32), mat_id=np.zeros(1, np.int32),
+                fibre=np.zeros((1, 2, 3)), dir_mask=np.zeros((4, 4), np.uint8),
+                neu_faces=np.zeros((0, 3), np.int32), materials=mooney_rivlin(c10, c01, 1.0e3, rho))
+    c = 1.0 / (0.625 * 0.01 ** 2)
+    P = O.Problem(mesh, O.Options(inertia_coef=c))
+    a = np.array([0.3, -0.7, 0.2])
+    hist = np.zeros((4, 3))
+    hist[0] = -a
+    R = P.residual(np.zeros((4, 4)), hist=hist)
+    V = 1.0 / 6.0
+    want = np.outer([2.0, 1.0, 1.0, 1.0], rho * V * a / 20.0)
+    assert np.allclose(R[:, :3], want, rtol=1e-13, atol=0)
+    g = np.array([[-1.0, -1.0, -1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    tau = 2.0 / (4.0 * 2.0 * (c10 + c01))
+    assert np.allclose(R[:, 3], -tau * V * rho * (g @ a) / 4.0, rtol=1e-13, atol=1e-300)
