@@ -90,3 +90,38 @@ def test_plain_dn_diverges_where_aitken_converges(tiny_tube):
     assert rec[2] > rec[1] > rec[0]
     v, k = Cp.dn_solve(P, np.zeros((mesh.n_nodes, 4)), 0.16, 2.0, omega0=1.0, tol=1e-9, max_iter=40)
     assert k < 20
+
+
+def test_wall_at_rest_under_p0_is_the_dn_limit_for_any_added_mass(tiny_tube):
+    """The surrogate fluid acts on the displacement from the wall at rest d_ref:
+    if d_ref is the solid's equilibrium under the uniform pressure p0, that
+    state sees exactly p0, so it is the DN limit whatever the added mass (the
+    loop starts from the undeformed state; its first cycle loads the solid with
+    p0 + c w.d_ref, which the oracle's undamped Newton takes in one step for
+    c up to 1 on this tube)."""
+    mesh, P = tiny_tube
+    p0 = 0.16
+    v0, _ = P.newton(np.zeros((mesh.n_nodes, 4)), fext=P.external_force(p0), rtol=1e-12)
+    for c in (0.5, 1.0):
+        v, k = Cp.dn_solve(P, np.zeros((mesh.n_nodes, 4)), p0, c, d_ref=v0, omega0=0.3, tol=1e-11, max_iter=60)
+        assert np.abs(v - v0).max() <= 1e-8 * np.abs(v0).max()
+
+
+def test_stop_measure_is_the_root_mean_square_over_interface_nodes():
+    """|r_k| / sqrt(n_Gamma) (Sec. 5.1) is the RMS interface residual: the same
+    one-node problem copied onto 1, 4 and 25 nodes gives the same residual
+    history and the same number of cycles."""
+    rng = np.random.default_rng(4)
+    a = -2.0
+    b = rng.standard_normal(3)
+    runs = []
+    for n in (1, 4, 25):
+        rec = []
+        d, k, _ = Cp.aitken_fixed_point(lambda d: a * d + b, np.zeros((n, 3)), omega0=0.4, tol=1e-12,
+                                        record=rec)
+        runs.append((k, rec))
+    for k, rec in runs[1:]:
+        assert k == runs[0][0]
+        big = np.asarray(runs[0][1]) > 1e-10 * runs[0][1][0]      # above the rounding floor of the last cycle
+        assert np.allclose(np.asarray(rec)[big], np.asarray(runs[0][1])[big], rtol=1e-12, atol=0)
+    assert abs(runs[0][1][0] - np.linalg.norm(b)) <= 1e-14 * np.linalg.norm(b)
