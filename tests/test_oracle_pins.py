@@ -5,6 +5,8 @@ closed forms, invariances, textbook special cases, numerical derivatives and
 energies differentiated by sympy.  A plausible slip anywhere in the oracle
 (a dropped term, a sign, a transposed operand) breaks at least one of them.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import scipy.optimize as so
@@ -466,3 +468,64 @@ def test_greedy_colouring_spec():
     for e, t in enumerate(m.tets):
         earlier = {col[f] for a in t for f in node_elems[a] if f < e}
         assert set(range(col[e])) <= earlier
+
+
+# ---------------------------------------------------------------- further pins (mutation check)
+def test_characteristic_length_is_the_longest_edge():
+    """h_T (reading r7) is the largest vertex-to-vertex distance, whichever
+    edge it is: random tetrahedra and one whose longest edge is (2, 3)."""
+    from scipy.spatial.distance import pdist
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((40, 3))
+    tets = np.array([rng.choice(40, 4, replace=False) for _ in range(200)], np.int32)
+    D = X[tets[:, 1:]] - X[tets[:, :1]]
+    flip = np.linalg.det(D) < 0
+    tets[flip] = tets[flip][:, [0, 2, 1, 3]]          # positive orientation
+    X = np.vstack([X, [[0, 0, 0], [0, 1, 0], [-2, 0, 0], [2, 0, 1]]])   # |x3 - x2| = sqrt 17, the others <= sqrt 6
+    tets = np.vstack([tets, [[40, 41, 42, 43]]]).astype(np.int32)
+    _, _, h = O.p1_geometry(X, tets)
+    want = np.array([pdist(X[t]).max() for t in tets])
+    assert np.allclose(h, want, rtol=1e-15, atol=0)
+    assert abs(h[-1] - np.hypot(4.0, 1.0)) <= 1e-15
+
+
+def test_face_pressures_add_up_face_by_face(small_tube):
+    """Per-face dead pressures (the batched segments' loads): the load equals
+    the sum over faces of each face's pressure times the load of that face
+    alone under a unit uniform pressure."""
+    mesh = small_tube
+    P = O.Problem(mesh)
+    faces = mesh.neu_faces
+    fp = np.random.default_rng(13).uniform(0.5, 2.0, len(faces))
+    got = P.external_force(0.3, face_pressure=fp)
+    want = np.zeros_like(got)
+    for f in range(len(faces)):
+        P.mesh = dataclasses.replace(mesh, neu_faces=faces[f:f + 1])
+        want += 0.3 * fp[f] * P.external_force(1.0)
+    P.mesh = mesh
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-16)
+
+
+def test_mooney_rivlin_ignores_fibre_parameters(small_tube):
+    """The fibre terms belong to the artery model only: a Mooney-Rivlin
+    material with nonzero k1, k2 and fibre directions gives the residual of
+    the same material with k1 = 0."""
+    base = Material(0, 0.5, 0.1, 0.0, 1.0, 1.0e3, 0.0)
+    with_fibres = Material(0, 0.5, 0.1, 5.0, 2.0, 1.0e3, 0.0)
+    s = _smooth_state(small_tube, 14)
+    R = [O.Problem(dataclasses.replace(small_tube, materials=[m, m])).residual(s) for m in (base, with_fibres)]
+    assert np.array_equal(R[0], R[1])
+
+
+@pytest.mark.parametrize("pressure", [1.0e-4, 0.16])
+def test_newton_stops_at_the_first_relative_residual_below_rtol(pressure):
+    """Sec. 4.4 stop, relative reading r11: Newton returns the first iterate
+    with ||R|| <= rtol ||R_0|| (for both a tiny and a moderate load, so the
+    scale of R_0 does not matter)."""
+    mesh = artery_tube(n_theta=16, n_z=2, length=0.125)
+    P = O.Problem(mesh)
+    rec = []
+    v, k = P.newton(np.zeros((mesh.n_nodes, 4)), fext=P.external_force(pressure), rtol=1e-6, record=rec)
+    assert len(rec) == k + 1
+    assert rec[-1] <= 1e-6 * rec[0]
+    assert all(r > 1e-6 * rec[0] for r in rec[:-1])
