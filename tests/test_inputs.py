@@ -143,3 +143,31 @@ def test_bench_ramp_driver_counts_newton_and_krylov_cap_hits():
     for _ in range(13):
         drv.step()
     assert drv.k == 3 and drv.newton_cap_hits == 1
+
+
+def test_tube_fibres_and_boundary_conditions():
+    """Fibre directions (readings r1, r2): per element two unit vectors with
+    no radial part at the element centroid, at +alpha and -alpha from e_theta
+    towards e_z, alpha = 29 deg in the media (inner four layers) and 62 deg in
+    the adventitia.  Ends (reading r13): u_z fixed on both end planes, u_x
+    where x = 0 and u_y where y = 0 on them, nothing else, pressure free."""
+    mesh = artery_tube(n_theta=16, n_z=4, length=1.0, materials=artery_layers(1.0e3))
+    xc = mesh.X[mesh.tets].mean(axis=1)
+    th = np.arctan2(xc[:, 1], xc[:, 0])
+    e_r = np.stack([np.cos(th), np.sin(th), 0 * th], axis=1)
+    e_t = np.stack([-np.sin(th), np.cos(th), 0 * th], axis=1)
+    alpha = np.deg2rad(np.where(mesh.mat_id == 0, 29.0, 62.0))
+    layer_r = np.hypot(xc[:, 0], xc[:, 1])
+    assert (mesh.mat_id[layer_r < 1.13 * np.cos(np.pi / 16)] == 0).all() and (mesh.mat_id[layer_r > 1.13] == 1).all()
+    for i, sgn in ((0, 1.0), (1, -1.0)):
+        a = mesh.fibre[:, i, :]
+        assert np.allclose(np.linalg.norm(a, axis=1), 1.0, atol=1e-14)
+        assert np.abs(np.einsum("ei,ei->e", a, e_r)).max() <= 1e-14
+        assert np.allclose(np.einsum("ei,ei->e", a, e_t), np.cos(alpha), atol=1e-14)
+        assert np.allclose(a[:, 2], sgn * np.sin(alpha), atol=1e-14)
+    X, m = mesh.X, mesh.dir_mask
+    end = np.isclose(X[:, 2], 0.0) | np.isclose(X[:, 2], 1.0)
+    assert (m[:, 2] == end).all()
+    assert (m[:, 0] == (end & np.isclose(X[:, 0], 0.0, atol=1e-12))).all()
+    assert (m[:, 1] == (end & np.isclose(X[:, 1], 0.0, atol=1e-12))).all()
+    assert (m[:, 3] == 0).all()
