@@ -99,3 +99,19 @@ def test_bad_segment_tables_are_rejected_before_gpu_work(lib, seg, n_segments, m
     st = b.lib.fsi_solid_create(ctypes.byref(d), 1, mats, None, ctypes.byref(h))
     assert st == -1 and not h.value
     assert msg in b.lib.fsi_solid_last_error(None)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: importing the binding from a package copy whose
+    library was never built raises ImportError naming the missing file."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = os.path.join(ROOT, "paper_1312_5561_gb300")
+    dst = tmp_path / "paper_1312_5561_gb300"
+    shutil.copytree(pkg, dst, ignore=shutil.ignore_patterns("_lib", "__pycache__", "csrc"))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "try:\n    import paper_1312_5561_gb300.binding\nexcept ImportError as e:\n    print('IMPORT-ERROR', e)\n"
+            "else:\n    print('LOADED')\n") % str(tmp_path)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300, cwd=str(tmp_path))
+    assert "IMPORT-ERROR" in out.stdout and "libfsi_solid.so is missing" in out.stdout, out.stdout + out.stderr
