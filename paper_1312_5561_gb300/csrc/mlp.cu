@@ -10,6 +10,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -288,11 +290,26 @@ struct Mlp {
 
 namespace {
 
+template <typename T>
+void release(T*& q) {
+  if (q) cudaFree(q);
+  q = nullptr;
+}
+
+// Grows the per-sample buffers to n samples.  The old buffers are released
+// and the capacity cleared first, so a failed allocation (CudaError) leaves
+// the handle with no buffers rather than with freed ones; the next call
+// allocates again.
 void mlp_reserve(Mlp& M, int n) {
   if (n <= M.cap) return;
-  for (float* a : M.act) if (a) cudaFree(a);
-  for (void* q : {(void*)M.dz, (void*)M.dz2, (void*)M.rowloss, (void*)M.xb, (void*)M.hb, (void*)M.hb2})
-    if (q) cudaFree(q);
+  M.cap = 0;
+  for (float*& a : M.act) release(a);
+  release(M.dz);
+  release(M.dz2);
+  release(M.rowloss);
+  release(M.xb);
+  release(M.hb);
+  release(M.hb2);
   int wmax = 0;
   for (int s : M.sizes) wmax = std::max(wmax, s);
   M.act.assign(M.sizes.size(), nullptr);
@@ -391,13 +408,16 @@ fsi_status fsi_mlp_create(int32_t n_layers, const int32_t* sizes, uint64_t seed,
       cudaMalloc(&M->pb, sizeof(__nv_bfloat16) * off) != cudaSuccess ||
       cudaMalloc(&M->lossdev, sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
-    delete M;
+    fsi_mlp_destroy(reinterpret_cast<fsi_mlp_t>(M));   // frees what was allocated
     return FSI_ERR_OOM;
   }
-  cudaMemcpy(M->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
-  cudaMemset(M->m, 0, sizeof(float) * off);
-  cudaMemset(M->v, 0, sizeof(float) * off);
-  cudaMemset(M->g, 0, sizeof(float) * off);
+  if (cudaMemcpy(M->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(M->m, 0, sizeof(float) * off) != cudaSuccess || cudaMemset(M->v, 0, sizeof(float) * off) != cudaSuccess ||
+      cudaMemset(M->g, 0, sizeof(float) * off) != cudaSuccess) {
+    cudaGetLastError();
+    fsi_mlp_destroy(reinterpret_cast<fsi_mlp_t>(M));
+    return FSI_ERR_CUDA;
+  }
   *out = reinterpret_cast<fsi_mlp_t>(M);
   return FSI_OK;
 }
@@ -462,6 +482,12 @@ fsi_status fsi_mlp_forward(fsi_mlp_t h, const float* X, int32_t n, float* Y, int
   } catch (const fsi::CudaError& e) {
     M->err = e.msg;
     return FSI_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    M->err = "host allocation failed";
+    return FSI_ERR_OOM;
+  } catch (const std::exception& e) {
+    M->err = e.what();
+    return FSI_ERR_ARG;
   }
   return FSI_OK;
 }
@@ -490,6 +516,12 @@ fsi_status fsi_mlp_train_step(fsi_mlp_t h, const float* X, const float* T, int32
   } catch (const fsi::CudaError& e) {
     M->err = e.msg;
     return FSI_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    M->err = "host allocation failed";
+    return FSI_ERR_OOM;
+  } catch (const std::exception& e) {
+    M->err = e.what();
+    return FSI_ERR_ARG;
   }
   return FSI_OK;
 }

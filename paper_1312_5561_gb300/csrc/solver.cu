@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <numeric>
 
@@ -1237,6 +1238,10 @@ struct fsi_solid_s {
   catch (const std::bad_alloc&) {                            \
     fsi::set_error(hptr, "host allocation failed");          \
     return FSI_ERR_OOM;                                      \
+  }                                                          \
+  catch (const std::exception& e) {                          \
+    fsi::set_error(hptr, e.what());                          \
+    return FSI_ERR_ARG;                                      \
   }
 
 static inline Handle* H(fsi_solid_t h) { return reinterpret_cast<Handle*>(h); }
@@ -1300,6 +1305,9 @@ fsi_status fsi_solid_create(const fsi_mesh_desc* mesh, int32_t n_mat, const fsi_
   } catch (const std::bad_alloc&) {
     g_create_error = "host allocation failed";
     return FSI_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_create_error = e.what();
+    return FSI_ERR_ARG;
   }
 }
 
