@@ -306,15 +306,27 @@ void run_vcycle(Handle& h, cudaStream_t s) {
     return;
   }
   if (!h.vc_exec) {
+    FSI_CUDA_TRY(cudaStreamSynchronize(h.stream));
     Profiler* saved = g_prof;
     g_prof = nullptr;
     const long long l0 = g_launches;
     cudaGraph_t graph = nullptr;
-    FSI_CUDA_TRY(cudaStreamSynchronize(h.stream));
-    FSI_CUDA_TRY(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
-    if (f32) vcycle<float>(h, 0, h.stream); else vcycle<double>(h, 0, h.stream);
-    cudaError_t e = cudaStreamEndCapture(h.stream, &graph);
+    cudaError_t e = cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        if (f32) vcycle<float>(h, 0, h.stream); else vcycle<double>(h, 0, h.stream);
+      } catch (...) {
+        // a failure while capturing: end the capture so that the handle's
+        // stream stays usable, and restore the accounting, then report it
+        if (cudaStreamEndCapture(h.stream, &graph) == cudaSuccess && graph) cudaGraphDestroy(graph);
+        g_prof = saved;
+        g_launches = l0;
+        throw;
+      }
+      e = cudaStreamEndCapture(h.stream, &graph);
+    }
     g_prof = saved;
+    if (e != cudaSuccess && graph) cudaGraphDestroy(graph);
     FSI_CUDA_TRY(e);
     h.vc_kernels = g_launches - l0;
     g_launches = l0;
