@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -36,7 +37,7 @@ struct Profiler {
   size_t used = 0;
 };
 extern thread_local Profiler* g_prof;
-extern long long g_launches;
+extern std::atomic<long long> g_launches;   // kernels launched by this process
 void launch_begin(int cls, cudaStream_t s);
 void launch_end(cudaStream_t s);
 }  // namespace fsi

@@ -18,6 +18,7 @@
 // Dirichlet-Neumann coupling loop of Sec. 5.1-5.2 (dn_impl) runs Newton solves
 // under a surrogate fluid load.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -30,12 +31,16 @@
 namespace fsi {
 
 thread_local Profiler* g_prof = nullptr;
-long long g_launches = 0;
-static long long g_class_launches[KC_COUNT] = {0};
+std::atomic<long long> g_launches{0};
+// While this thread captures a V-cycle into a graph, its launches are recorded,
+// not run: they are counted here and added to g_launches per graph launch.
+static thread_local long long* t_captured = nullptr;
 
 void launch_begin(int cls, cudaStream_t s) {
-  ++g_launches;
-  if (cls >= 0 && cls < KC_COUNT) ++g_class_launches[cls];
+  if (t_captured)
+    ++*t_captured;
+  else
+    g_launches.fetch_add(1, std::memory_order_relaxed);
   Profiler* p = g_prof;
   if (!p || !p->on) return;
   if (p->pool.size() < 2 * (p->used + 1)) {
@@ -309,33 +314,34 @@ void run_vcycle(Handle& h, cudaStream_t s) {
     FSI_CUDA_TRY(cudaStreamSynchronize(h.stream));
     Profiler* saved = g_prof;
     g_prof = nullptr;
-    const long long l0 = g_launches;
+    long long captured = 0;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+      t_captured = &captured;
       try {
         if (f32) vcycle<float>(h, 0, h.stream); else vcycle<double>(h, 0, h.stream);
       } catch (...) {
         // a failure while capturing: end the capture so that the handle's
         // stream stays usable, and restore the accounting, then report it
+        t_captured = nullptr;
         if (cudaStreamEndCapture(h.stream, &graph) == cudaSuccess && graph) cudaGraphDestroy(graph);
         g_prof = saved;
-        g_launches = l0;
         throw;
       }
+      t_captured = nullptr;
       e = cudaStreamEndCapture(h.stream, &graph);
     }
     g_prof = saved;
     if (e != cudaSuccess && graph) cudaGraphDestroy(graph);
     FSI_CUDA_TRY(e);
-    h.vc_kernels = g_launches - l0;
-    g_launches = l0;
+    h.vc_kernels = captured;
     e = cudaGraphInstantiate(&h.vc_exec, graph, 0);
     cudaGraphDestroy(graph);
     FSI_CUDA_TRY(e);
   }
   FSI_CUDA_TRY(cudaGraphLaunch(h.vc_exec, s));
-  g_launches += h.vc_kernels;
+  g_launches.fetch_add(h.vc_kernels, std::memory_order_relaxed);
 }
 
 void apply_operator(Handle& h, const double* x, double* y, cudaStream_t s);
@@ -1517,7 +1523,7 @@ fsi_status fsi_solid_get_levels(fsi_solid_t hh, int32_t* nodes_out, int32_t* blo
   return FSI_OK;
 }
 
-int64_t fsi_solid_launch_count(void) { return (int64_t)fsi::g_launches; }
+int64_t fsi_solid_launch_count(void) { return (int64_t)fsi::g_launches.load(std::memory_order_relaxed); }
 
 fsi_status fsi_solid_kernel_timing(fsi_solid_t hh, int32_t enable, double* ms_out, int64_t* launches_out) {
   Handle* h = H(hh);
