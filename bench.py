@@ -525,7 +525,7 @@ def oracle_residual_check(args, verify_path, pressure):
 
 
 # ------------------------------------------------------------------ main
-def main():
+def make_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -557,7 +557,11 @@ def main():
                     help="AMG aggregation (default: grow for the 16-layer refined tube, ring otherwise)")
     ap.add_argument("--compare-paper-solver", action="store_true",
                     help="also time BiCGStab + P_L (the paper's solid solver) on the same workload")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = make_parser().parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -171,3 +171,25 @@ def test_tube_fibres_and_boundary_conditions():
     assert (m[:, 0] == (end & np.isclose(X[:, 0], 0.0, atol=1e-12))).all()
     assert (m[:, 1] == (end & np.isclose(X[:, 1], 0.0, atol=1e-12))).all()
     assert (m[:, 3] == 0).all()
+
+
+def test_bench_default_is_the_documented_headline_configuration():
+    """`python bench.py` with no flags times the refined tube (128 x 16 x 256
+    hexahedra, kappa = 1e5 c10) in FP32 + refinement with grown aggregates,
+    FGMRES to 1e-8 (Krylov cap 600) and the library's default smoothers; the
+    plain-FP64 arm differs only in precision; `--config tube` switches to ring
+    aggregates on the 393k tube at kappa = 1e3 c10."""
+    sys.path.insert(0, ROOT)
+    import bench
+    args = bench.make_parser().parse_args([])
+    assert (args.config, args.precision, args.gpus, args.steps >= 10, args.warmup >= 3) == \
+        ("refined", "fp32", 1, True, True)
+    assert bench._workload_geometry(args) == (128, 16, 256, 1.0e5)
+    o = bench.solver_options(args)
+    assert o == dict(precision=1, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=1, amg_lag=0, max_krylov=600,
+                     aggregation=1, segment_krylov=1)
+    args.precision = "fp64"
+    assert bench.solver_options(args) == dict(o, precision=0)
+    tube = bench.make_parser().parse_args(["--config", "tube"])
+    assert bench._workload_geometry(tube) == (64, 8, 128, 1.0e3)
+    assert bench.solver_options(tube)["aggregation"] == 0
