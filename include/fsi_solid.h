@@ -111,7 +111,9 @@ enum { FSI_PRECOND_AMG = 0, FSI_PRECOND_BLOCK_LT = 1 };
  *                Frobenius norm), leftovers join their strongest neighbour's
  *                aggregate (default).
  *  FSI_AGG_GROW  an aggregate grows one node at a time by the strongest
- *                connection from any member, up to 8 nodes: on walls meshed
+ *                connection from any member, up to 8 nodes, and leftovers
+ *                join as with FSI_AGG_RING (so an aggregate may end with a
+ *                few more): on walls meshed
  *                with many thin element layers it forms lines across the wall,
  *                where FSI_AGG_RING coarsens along the weak directions and the
  *                Krylov iteration stalls. */
