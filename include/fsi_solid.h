@@ -186,6 +186,13 @@ typedef struct {
                                products, Hessenberg matrices and stop, so each segment
                                stops at its own convergence); 0 = one process over the
                                union (the segments' right-hand sides scaled to unit norm) */
+  int32_t exact_candidates; /* coarse near-null space of the aggregation hierarchy: 1 = the
+                               full R factor of each aggregate's QR, so that the tentative
+                               prolongator reproduces the rigid-body modes and constant
+                               pressure exactly on the free unknowns (P_t B_c = B) also where
+                               a mode depends on the others within an aggregate (end planes
+                               with u_z fixed); 0 (default) = such a mode is dropped from the
+                               coarse space of that aggregate altogether */
 } fsi_solver_opts;
 
 /* Load of one solve (device arrays owned by the caller; NULL = absent).

@@ -60,7 +60,8 @@ class SolverOpts(C.Structure):
                 ("fibre_factor", C.c_double), ("inertia_coef", C.c_double), ("amg_lag", C.c_int32),
                 ("assembly", C.c_int32), ("precond", C.c_int32), ("schur_theta", C.c_double),
                 ("vanka_omega", C.c_double), ("aggregation", C.c_int32), ("coarse_bf16", C.c_int32),
-                ("coarse_smoother", C.c_int32), ("autotune", C.c_int32), ("segment_krylov", C.c_int32)]
+                ("coarse_smoother", C.c_int32), ("autotune", C.c_int32), ("segment_krylov", C.c_int32),
+                ("exact_candidates", C.c_int32)]
 
 
 class LoadDesc(C.Structure):

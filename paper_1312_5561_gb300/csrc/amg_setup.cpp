@@ -324,7 +324,7 @@ void block_inverses(const HostBsr& A, std::vector<double>& Dinv) {
 
 void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
                         const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap, bool filter,
-                        std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow) {
+                        std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow, bool exact_candidates) {
   levels.clear();
   levels.emplace_back();
   levels[0].A = A0;
@@ -411,8 +411,11 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
           for (int r = 0; r < rows; ++r) Q[(size_t)r * NS + c] /= nn;
           R[c * NS + c] = nn;
         } else {
+          // dependent column: no basis vector; with exact candidates its
+          // projections on the earlier columns stay in R, so Q R = B still
           for (int r = 0; r < rows; ++r) Q[(size_t)r * NS + c] = 0.0;
-          for (int k = 0; k < c; ++k) R[k * NS + c] = 0.0;
+          if (!exact_candidates)
+            for (int k = 0; k < c; ++k) R[k * NS + c] = 0.0;
           R[c * NS + c] = 0.0;
         }
       }

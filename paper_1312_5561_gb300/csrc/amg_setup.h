@@ -48,8 +48,13 @@ struct HostCoarse {
 // couplings (needed when inertia dominates the displacement block: the PSPG
 // inertia coupling then blows up the pressure rows of D^-1 A).
 // grow: aggregates grow along the strongest connections (see aggregate_capped).
+// exact_candidates: the coarse near-null space is the whole R factor of each
+// aggregate's QR (P_t B_c = B on the free unknowns); otherwise a column that
+// depends on the earlier ones within an aggregate is dropped with its
+// projections.
 void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
                         const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap, bool filter,
-                        std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow = false);
+                        std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow = false,
+                        bool exact_candidates = false);
 
 }  // namespace fsi

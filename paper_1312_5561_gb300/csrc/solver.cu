@@ -206,7 +206,7 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
   HostCoarse hc;
   h.filter_p = h.opts.inertia_coef > 0.0;
   build_sa_hierarchy(A0, free0, X, comp0, std::max(1, h.opts.coarse_max_nodes), std::max(1, h.opts.max_levels),
-                     8, h.filter_p, hl, hc, h.opts.aggregation == FSI_AGG_GROW);
+                     8, h.filter_p, hl, hc, h.opts.aggregation == FSI_AGG_GROW, h.opts.exact_candidates != 0);
   const int nl = (int)hl.size();
   const size_t ts = f32 ? 4 : 8;
   for (int l = 1; l < nl; ++l) {
@@ -1285,6 +1285,7 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->coarse_smoother = FSI_COARSE_MR;
   o->autotune = 1;
   o->segment_krylov = 1;
+  o->exact_candidates = 0;
   o->coarse_max_nodes = 16;
   o->max_levels = 12;
   o->use_pspg = 1;

@@ -4,7 +4,7 @@
 // together with an FNV-1a hash over every level array, so that a test can
 // compare runs at different thread counts and check the products with scipy.
 //
-//   host_amg_setup_main <dir> <ring|grow>
+//   host_amg_setup_main <dir> <ring|grow> [exact]
 //
 // <dir>/dims.bin: int64 n, nb; rp.bin int32[n+1]; ci.bin int32[nb];
 // v.bin double[nb*16]; free.bin uint8[n*4]; X.bin double[n*3].
@@ -47,6 +47,7 @@ int main(int argc, char** argv) {
   }
   const std::string d = argv[1];
   const bool grow = std::string(argv[2]) == "grow";
+  const bool exact = argc > 3 && std::string(argv[3]) == "exact";
   try {
     const auto dims = read_raw<int64_t>(d + "/dims.bin", 2);
     const int n = (int)dims[0], nb = (int)dims[1];
@@ -61,7 +62,7 @@ int main(int argc, char** argv) {
     const std::vector<int32_t> comp(n, 0);
     std::vector<HostLevel> L;
     HostCoarse C;
-    build_sa_hierarchy(A, fr, X.data(), comp, 16, 12, 8, false, L, C, grow);
+    build_sa_hierarchy(A, fr, X.data(), comp, 16, 12, 8, false, L, C, grow, exact);
     uint64_t h = 1469598103934665603ull;
     for (const auto& l : L) {
       h = fnv(l.A.rp, h); h = fnv(l.A.ci, h); h = fnv(l.A.v, h); h = fnv(l.free, h); h = fnv(l.Dinv, h);
@@ -73,7 +74,7 @@ int main(int argc, char** argv) {
     }
     h = fnv(C.comp_ptr, h);
     h = fnv(C.inv_off, h);
-    for (int k = 0; k < 2 && k < (int)L.size(); ++k) {
+    for (int k = 0; k < 3 && k < (int)L.size(); ++k) {
       const std::string p = d + "/l" + std::to_string(k) + "_";
       const HostLevel& l = L[k];
       write_raw(p + "A_rp.bin", l.A.rp);

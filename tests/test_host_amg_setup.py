@@ -49,9 +49,10 @@ def problem(tmp_path_factory):
     return dict(dir=d, n=n, K=K.tocsr(), free=free.ravel(), X=mesh.X)
 
 
-def _run(exe, d, mode, threads):
+def _run(exe, d, mode, threads, exact=False):
     env = dict(os.environ, OMP_NUM_THREADS=str(threads))
-    out = subprocess.run([exe, d, mode], capture_output=True, text=True, env=env, timeout=300)
+    out = subprocess.run([exe, d, mode] + (["exact"] if exact else []), capture_output=True, text=True, env=env,
+                         timeout=300)
     assert out.returncode == 0, out.stderr
     nlev, n1, h = out.stdout.split()
     return int(nlev), int(n1), h
@@ -76,63 +77,94 @@ def test_hierarchy_is_the_same_at_any_thread_count(exe, problem, mode):
     assert runs[1] == runs[0] and runs[2] == runs[0]
 
 
-@pytest.mark.parametrize("mode", ["ring", "grow"])
-def test_levels_0_and_1_follow_the_smoothed_aggregation_definitions(exe, problem, mode):
-    d, n = problem["dir"], problem["n"]
-    _, nc, _ = _run(exe, d, mode, 3)
-    A0 = problem["K"]
-    free0 = problem["free"].astype(np.float64)
-    F = sp.diags(free0)
-    # diagonal block inverses
-    Dinv = _read(d, "l0_Dinv.bin", np.float64).reshape(n, 4, 4)
-    Dblk = np.stack([A0[4 * i:4 * i + 4, 4 * i:4 * i + 4].toarray() for i in range(n)])
-    assert np.abs(np.einsum("nij,njk->nik", Dblk, Dinv) - np.eye(4)).max() <= 1e-10
-    # aggregates: every node in one aggregate, every aggregate used and connected
-    # in the block graph of A (roots take up to 7 neighbours, leftover nodes join
-    # a neighbouring aggregate), about 8 nodes per aggregate
-    agg = _read(d, "l0_agg.bin", np.int32)
-    assert agg.size == n and agg.min() == 0 and agg.max() == nc - 1
-    assert np.bincount(agg, minlength=nc).min() >= 1 and 4.0 <= n / nc <= 9.0
-    Gb = sp.csr_matrix((np.ones(A0.nnz), A0.indices // 4, A0.indptr[::4]), shape=(n, n)).tocoo()
-    keep = agg[Gb.row] == agg[Gb.col]
-    inner = sp.csr_matrix((np.ones(keep.sum()), (Gb.row[keep], Gb.col[keep])), shape=(n, n))
-    assert sp.csgraph.connected_components(inner, directed=False)[0] == nc
-    # tentative prolongator: one 4 x 7 block per node in its aggregate's column,
-    # orthonormal columns per aggregate (dependent ones dropped), and the rigid
-    # body modes + constant pressure on the free rows lie in its range
-    Ptv = _read(d, "l0_Pt.bin", np.float64).reshape(n, 4, NS)
-    rows = (4 * np.arange(n)[:, None, None] + np.arange(4)[None, :, None]).repeat(NS, 2)
-    cols = (NS * agg[:, None, None] + np.arange(NS)[None, None, :]).repeat(4, 1)
-    Pt = sp.csr_matrix((Ptv.ravel(), (rows.ravel(), cols.ravel())), shape=(4 * n, NS * nc))
-    G = (Pt.T @ Pt).toarray()
-    g = np.diag(G)
-    assert np.all((np.abs(g - 1.0) <= 1e-12) | (np.abs(g) <= 1e-12))
-    assert np.abs(G - np.diag(g)).max() <= 1e-12
-    X = problem["X"] - problem["X"].mean(axis=0)
-    B = np.zeros((n, 4, NS))
+def _rigid_modes(X):
+    """Level-0 near-null space per node [n, 4, 7]: translations, rotations about
+    the centroid, constant pressure."""
+    X = X - X.mean(axis=0)
+    B = np.zeros((len(X), 4, NS))
     B[:, 0, 0] = B[:, 1, 1] = B[:, 2, 2] = B[:, 3, 6] = 1.0
     x, y, z = X[:, 0], X[:, 1], X[:, 2]
     B[:, 1, 3], B[:, 2, 3] = -z, y          # rotation about x: e_x x r
     B[:, 0, 4], B[:, 2, 4] = z, -x          # about y
     B[:, 0, 5], B[:, 1, 5] = -y, x          # about z
-    FB = F @ B.reshape(4 * n, NS)
-    assert np.abs(FB - Pt @ (Pt.T @ FB)).max() <= 1e-10 * np.abs(FB).max()
-    # smoothing weight omega = 4 / (3 lambda), lambda a power-iteration estimate of
-    # the spectral radius of D^-1 A on the free unknowns (20 steps: within 0.8-1.05
-    # of it; 0.91 here, where the top three eigenvalues lie within 2 %)
-    omega = _read(d, "l0_omega.bin", np.float64)[0]
-    Dm = sp.csr_matrix(sp.block_diag(list(Dinv), format="csr"))
-    rho = np.abs(sla.eigs(F @ Dm @ A0 @ F, k=3, which="LM", return_eigenvectors=False, tol=1e-8)).max()
+    return B
+
+
+def _check_level(d, l, A, b, B, exact):
+    """Definitions of one smoothed-aggregation level l (block size b, operator A,
+    near-null space B [n, b, 7] of this level); returns P_t, F, the number of
+    coarse nodes and the next level's operator."""
+    n = A.shape[0] // b
+    free = _read(d, f"l{l}_free.bin", np.uint8).astype(np.float64)
+    F = sp.diags(free)
+    # diagonal block inverses
+    Dinv = _read(d, f"l{l}_Dinv.bin", np.float64).reshape(n, b, b)
+    Ab = A.tobsr(blocksize=(b, b))
+    Ab.sort_indices()
+    rows = np.repeat(np.arange(n), np.diff(Ab.indptr))
+    Dblk = np.zeros((n, b, b))
+    Dblk[rows[Ab.indices == rows]] = Ab.data[Ab.indices == rows]
+    assert np.abs(np.einsum("nij,njk->nik", Dblk, Dinv) - np.eye(b)).max() <= 1e-9
+    # aggregates: every node in one aggregate, every aggregate used and connected
+    # in the block graph of A (roots take up to 7 neighbours, leftover nodes join
+    # a neighbouring aggregate), about 8 nodes per aggregate
+    agg = _read(d, f"l{l}_agg.bin", np.int32)
+    nc = int(agg.max()) + 1
+    assert agg.size == n and agg.min() == 0
+    assert np.bincount(agg, minlength=nc).min() >= 1 and 4.0 <= n / nc <= 9.0
+    keep = agg[rows] == agg[Ab.indices]
+    inner = sp.csr_matrix((np.ones(keep.sum()), (rows[keep], Ab.indices[keep])), shape=(n, n))
+    assert sp.csgraph.connected_components(inner, directed=False)[0] == nc
+    # tentative prolongator: one b x 7 block per node in its aggregate's column,
+    # orthonormal columns per aggregate (dependent ones dropped)
+    Ptv = _read(d, f"l{l}_Pt.bin", np.float64).reshape(n, b, NS)
+    r_ = (b * np.arange(n)[:, None, None] + np.arange(b)[None, :, None]).repeat(NS, 2)
+    c_ = (NS * agg[:, None, None] + np.arange(NS)[None, None, :]).repeat(b, 1)
+    Pt = sp.csr_matrix((Ptv.ravel(), (r_.ravel(), c_.ravel())), shape=(b * n, NS * nc))
+    G = (Pt.T @ Pt).toarray()
+    g = np.diag(G)
+    assert np.all((np.abs(g - 1.0) <= 1e-12) | (np.abs(g) <= 1e-12))
+    assert np.abs(G - np.diag(g)).max() <= 1e-12
+    # the near-null space on the free unknowns lies in its range: on level 0
+    # always; on coarser levels when the coarse candidates are the whole R
+    # factor (exact), since otherwise a column that was dependent in a finer
+    # aggregate is dropped from the candidates of that aggregate
+    FB = F @ B.reshape(b * n, NS)
+    if l == 0 or exact:
+        assert np.abs(FB - Pt @ (Pt.T @ FB)).max() <= 1e-9 * np.abs(FB).max()
+    # smoothing weight omega = 4 / (3 lambda), lambda a 20-step power-iteration
+    # estimate of the spectral radius of D^-1 A on the free unknowns
+    omega = _read(d, f"l{l}_omega.bin", np.float64)[0]
+    Dm = sp.bsr_matrix((Dinv, np.arange(n), np.arange(n + 1)), shape=(b * n, b * n)).tocsr()
+    rho = np.abs(sla.eigs(F @ Dm @ A @ F, k=3, which="LM", return_eigenvectors=False, tol=1e-8)).max()
     assert 0.8 * rho <= 4.0 / (3.0 * omega) <= 1.05 * rho
     # smoothed prolongator P = F (I - omega D^-1 A) Pt
-    P = _bsr(d, "l0_P", n, nc, 4, NS)
-    Pref = F @ (Pt - omega * (Dm @ (A0 @ Pt)))
+    P = _bsr(d, f"l{l}_P", n, nc, b, NS)
+    Pref = F @ (Pt - omega * (Dm @ (A @ Pt)))
     assert abs(P - Pref).max() <= 1e-12 * abs(Pref).max()
-    # Galerkin coarse operator A1 = P^T A0 P, identity rows for unknowns with no fine support
-    A1 = _bsr(d, "l1_A", nc, nc, NS, NS)
-    free1 = _read(d, "l1_free.bin", np.uint8).astype(np.float64)
-    assert free1.size == NS * nc
+    # Galerkin coarse operator A_(l+1) = P^T A P, identity rows for unknowns with no fine support
+    A1 = _bsr(d, f"l{l + 1}_A", nc, nc, NS, NS)
+    free1 = _read(d, f"l{l + 1}_free.bin", np.uint8).astype(np.float64)
     empty = np.asarray(abs(P).sum(axis=0)).ravel() == 0.0
     assert np.array_equal(free1 == 0.0, empty)
-    Aref = (P.T @ A0 @ P) + sp.diags(1.0 - free1)
+    Aref = (P.T @ A @ P) + sp.diags(1.0 - free1)
     assert abs(A1 - Aref).max() <= 1e-12 * abs(Aref).max()
+    return Pt, F, nc, A1
+
+
+@pytest.mark.parametrize("exact", [False, True], ids=["default", "exact"])
+@pytest.mark.parametrize("mode", ["ring", "grow"])
+def test_levels_0_and_1_follow_the_smoothed_aggregation_definitions(exe, problem, mode, exact):
+    """Levels 0 (4 x 4 blocks) and 1 (7 x 7 blocks): block inverses, connected
+    aggregates, orthonormal tentative prolongator holding the near-null space,
+    omega from the spectral radius of D^-1 A, P = F (I - omega D^-1 A) P_t and
+    the Galerkin product; the level-1 candidates are P_t^T F B of level 0."""
+    d, n = problem["dir"], problem["n"]
+    nlev, _, _ = _run(exe, d, mode, 3, exact)
+    assert nlev >= 3
+    A0 = problem["K"]
+    assert abs(_bsr(d, "l0_A", n, n, 4, 4) - A0).max() == 0.0
+    B0 = _rigid_modes(problem["X"])
+    Pt0, F0, nc, A1 = _check_level(d, 0, A0, 4, B0, exact)
+    B1 = (Pt0.T @ (F0 @ B0.reshape(4 * n, NS))).reshape(nc, NS, NS)
+    _check_level(d, 1, A1, NS, B1, exact)
