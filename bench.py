@@ -87,6 +87,8 @@ def solver_options(args):
     if args.coarse_jacobi:
         kry.update(coarse_smoother=0, nu_coarse=1)
     kry.update(segment_krylov=int(args.segment_krylov))
+    if args.exact_candidates:
+        kry.update(exact_candidates=1)
     if args.nu_finest > 0 and args.smoother != "vanka":
         kry.update(nu_pre=args.nu_finest, nu_post=args.nu_finest)
     return dict(precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=int(args.graphs),
@@ -555,6 +557,8 @@ def make_parser():
                     help="damped block Jacobi (1+1) on the coarse levels instead of minimal-residual block Jacobi")
     ap.add_argument("--aggregation", default=None, choices=["ring", "grow"],
                     help="AMG aggregation (default: grow for the 16-layer refined tube, ring otherwise)")
+    ap.add_argument("--exact-candidates", action="store_true",
+                    help="coarse near-null space from the whole QR factor of each aggregate (opts.exact_candidates)")
     ap.add_argument("--compare-paper-solver", action="store_true",
                     help="also time BiCGStab + P_L (the paper's solid solver) on the same workload")
     return ap
@@ -635,6 +639,8 @@ def main():
                                         else "minimal-residual block Jacobi 2+2"),
                        coarse_operators="BF16 (V-cycle reads)" if args.coarse_bf16 else "FP32",
                        aggregation=aggregation_of(args),
+                       coarse_candidates=("whole QR factor" if args.exact_candidates else
+                                          "QR factor without dependent columns"),
                        krylov=("per-segment FGMRES (one Arnoldi process per segment)"
                                if args.config == "batched" and args.segment_krylov and args.solver != "bicgstab-pl"
                                else None),
