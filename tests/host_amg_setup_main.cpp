@@ -88,6 +88,10 @@ int main(int argc, char** argv) {
         write_raw(p + "P_rp.bin", l.P.rp);
         write_raw(p + "P_ci.bin", l.P.ci);
         write_raw(p + "P_v.bin", l.P.v);
+        write_raw(p + "PT_rp.bin", l.PT.rp);
+        write_raw(p + "PT_ci.bin", l.PT.ci);
+        write_raw(p + "PT_v.bin", l.PT.v);
+        write_raw(p + "pt_src.bin", l.pt_src);
         write_raw(p + "omega.bin", std::vector<double>{l.omega_p});
       }
     }

@@ -142,6 +142,14 @@ def _check_level(d, l, A, b, B, exact):
     P = _bsr(d, f"l{l}_P", n, nc, b, NS)
     Pref = F @ (Pt - omega * (Dm @ (A @ Pt)))
     assert abs(P - Pref).max() <= 1e-12 * abs(Pref).max()
+    # the stored transpose used by the restriction: PT = P^T exactly, and its
+    # block t is the transpose of P block pt_src[t]
+    PT = _bsr(d, f"l{l}_PT", nc, n, NS, b)
+    assert abs(PT - P.T).max() == 0.0
+    pt_src = _read(d, f"l{l}_pt_src.bin", np.int32)
+    Pv = _read(d, f"l{l}_P_v.bin", np.float64).reshape(-1, b, NS)
+    PTv = _read(d, f"l{l}_PT_v.bin", np.float64).reshape(-1, NS, b)
+    assert np.array_equal(PTv, np.transpose(Pv[pt_src], (0, 2, 1)))
     # Galerkin coarse operator A_(l+1) = P^T A P, identity rows for unknowns with no fine support
     A1 = _bsr(d, f"l{l + 1}_A", nc, nc, NS, NS)
     free1 = _read(d, f"l{l + 1}_free.bin", np.uint8).astype(np.float64)
