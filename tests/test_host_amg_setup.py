@@ -49,10 +49,10 @@ def problem(tmp_path_factory):
     return dict(dir=d, n=n, K=K.tocsr(), free=free.ravel(), X=mesh.X)
 
 
-def _run(exe, d, mode, threads, exact=False):
+def _run(exe, d, mode, threads, exact=False, filt=False):
     env = dict(os.environ, OMP_NUM_THREADS=str(threads))
-    out = subprocess.run([exe, d, mode] + (["exact"] if exact else []), capture_output=True, text=True, env=env,
-                         timeout=300)
+    flags = (["exact"] if exact else []) + (["filter"] if filt else [])
+    out = subprocess.run([exe, d, mode] + flags, capture_output=True, text=True, env=env, timeout=300)
     assert out.returncode == 0, out.stderr
     nlev, n1, h = out.stdout.split()
     return int(nlev), int(n1), h
@@ -90,7 +90,26 @@ def _rigid_modes(X):
     return B
 
 
-def _check_level(d, l, A, b, B, exact):
+def _filter_up(A, b):
+    """A without the couplings between the displacement-like unknowns (first
+    b - 1 of a block) and the pressure-like last one of each block."""
+    A = A.tocoo()
+    keep = (A.row % b == b - 1) == (A.col % b == b - 1)
+    return sp.csr_matrix((A.data[keep], (A.row[keep], A.col[keep])), shape=A.shape)
+
+
+def _block_diag_inverse(A, b):
+    n = A.shape[0] // b
+    Ab = A.tobsr(blocksize=(b, b))
+    Ab.sort_indices()
+    rows = np.repeat(np.arange(n), np.diff(Ab.indptr))
+    D = np.zeros((n, b, b))
+    D[rows[Ab.indices == rows]] = Ab.data[Ab.indices == rows]
+    Dinv = np.linalg.inv(D)
+    return sp.bsr_matrix((Dinv, np.arange(n), np.arange(n + 1)), shape=(b * n, b * n)).tocsr()
+
+
+def _check_level(d, l, A, b, B, exact, filt=False):
     """Definitions of one smoothed-aggregation level l (block size b, operator A,
     near-null space B [n, b, 7] of this level); returns P_t, F, the number of
     coarse nodes and the next level's operator."""
@@ -132,15 +151,19 @@ def _check_level(d, l, A, b, B, exact):
     FB = F @ B.reshape(b * n, NS)
     if l == 0 or exact:
         assert np.abs(FB - Pt @ (Pt.T @ FB)).max() <= 1e-9 * np.abs(FB).max()
+    # smoothing operator S: A itself, or (filt: the inertia case) A without its
+    # displacement-pressure couplings, with its own block diagonal D_S
+    S = _filter_up(A, b) if filt else A
+    Dm = _block_diag_inverse(S, b) if filt else \
+        sp.bsr_matrix((Dinv, np.arange(n), np.arange(n + 1)), shape=(b * n, b * n)).tocsr()
     # smoothing weight omega = 4 / (3 lambda), lambda a 20-step power-iteration
-    # estimate of the spectral radius of D^-1 A on the free unknowns
+    # estimate of the spectral radius of D_S^-1 S on the free unknowns
     omega = _read(d, f"l{l}_omega.bin", np.float64)[0]
-    Dm = sp.bsr_matrix((Dinv, np.arange(n), np.arange(n + 1)), shape=(b * n, b * n)).tocsr()
-    rho = np.abs(sla.eigs(F @ Dm @ A @ F, k=3, which="LM", return_eigenvectors=False, tol=1e-8)).max()
+    rho = np.abs(sla.eigs(F @ Dm @ S @ F, k=3, which="LM", return_eigenvectors=False, tol=1e-8)).max()
     assert 0.8 * rho <= 4.0 / (3.0 * omega) <= 1.05 * rho
-    # smoothed prolongator P = F (I - omega D^-1 A) Pt
+    # smoothed prolongator P = F (I - omega D_S^-1 S) Pt
     P = _bsr(d, f"l{l}_P", n, nc, b, NS)
-    Pref = F @ (Pt - omega * (Dm @ (A @ Pt)))
+    Pref = F @ (Pt - omega * (Dm @ (S @ Pt)))
     assert abs(P - Pref).max() <= 1e-12 * abs(Pref).max()
     # the stored transpose used by the restriction: PT = P^T exactly, and its
     # block t is the transpose of P block pt_src[t]
@@ -176,3 +199,16 @@ def test_levels_0_and_1_follow_the_smoothed_aggregation_definitions(exe, problem
     Pt0, F0, nc, A1 = _check_level(d, 0, A0, 4, B0, exact)
     B1 = (Pt0.T @ (F0 @ B0.reshape(4 * n, NS))).reshape(nc, NS, NS)
     _check_level(d, 1, A1, NS, B1, exact)
+
+
+def test_filtered_prolongator_smoothing(exe, problem):
+    """The inertia case: the prolongator is smoothed with A minus its
+    displacement-pressure couplings, D and omega taken from that operator;
+    the Galerkin products still use A itself."""
+    d, n = problem["dir"], problem["n"]
+    _run(exe, d, "ring", 3, filt=True)
+    A0 = problem["K"]
+    B0 = _rigid_modes(problem["X"])
+    Pt0, F0, nc, A1 = _check_level(d, 0, A0, 4, B0, False, filt=True)
+    B1 = (Pt0.T @ (F0 @ B0.reshape(4 * n, NS))).reshape(nc, NS, NS)
+    _check_level(d, 1, A1, NS, B1, False, filt=True)
