@@ -89,6 +89,8 @@ def solver_options(args):
     kry.update(segment_krylov=int(args.segment_krylov))
     if args.exact_candidates:
         kry.update(exact_candidates=1)
+    if args.power_steps != 20:
+        kry.update(power_steps=args.power_steps)
     if args.nu_finest > 0 and args.smoother != "vanka":
         kry.update(nu_pre=args.nu_finest, nu_post=args.nu_finest)
     return dict(precision=prec, newton_rtol=1e-8, krylov_rtol=1e-8, use_graphs=int(args.graphs),
@@ -559,6 +561,8 @@ def make_parser():
                     help="AMG aggregation (default: grow for the 16-layer refined tube, ring otherwise)")
     ap.add_argument("--exact-candidates", action="store_true",
                     help="coarse near-null space from the whole QR factor of each aggregate (opts.exact_candidates)")
+    ap.add_argument("--power-steps", type=int, default=20,
+                    help="power-iteration steps for lambda_max(D^-1 A) of each AMG level (opts.power_steps)")
     ap.add_argument("--compare-paper-solver", action="store_true",
                     help="also time BiCGStab + P_L (the paper's solid solver) on the same workload")
     return ap
@@ -641,6 +645,7 @@ def main():
                        aggregation=aggregation_of(args),
                        coarse_candidates=("whole QR factor" if args.exact_candidates else
                                           "QR factor without dependent columns"),
+                       power_steps=args.power_steps,
                        krylov=("per-segment FGMRES (one Arnoldi process per segment)"
                                if args.config == "batched" and args.segment_krylov and args.solver != "bicgstab-pl"
                                else None),

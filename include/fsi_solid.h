@@ -193,6 +193,10 @@ typedef struct {
                                a mode depends on the others within an aggregate (end planes
                                with u_z fixed); 0 (default) = such a mode is dropped from the
                                coarse space of that aggregate altogether */
+  int32_t power_steps;      /* steps of the power iteration estimating lambda_max(D^-1 A) of
+                               each level for the prolongator smoothing weight 4/(3 lambda)
+                               (default 20; more steps give a closer, larger estimate where
+                               the top eigenvalues cluster, hence a smaller weight) */
 } fsi_solver_opts;
 
 /* Load of one solve (device arrays owned by the caller; NULL = absent).

@@ -61,7 +61,7 @@ class SolverOpts(C.Structure):
                 ("assembly", C.c_int32), ("precond", C.c_int32), ("schur_theta", C.c_double),
                 ("vanka_omega", C.c_double), ("aggregation", C.c_int32), ("coarse_bf16", C.c_int32),
                 ("coarse_smoother", C.c_int32), ("autotune", C.c_int32), ("segment_krylov", C.c_int32),
-                ("exact_candidates", C.c_int32)]
+                ("exact_candidates", C.c_int32), ("power_steps", C.c_int32)]
 
 
 class LoadDesc(C.Structure):

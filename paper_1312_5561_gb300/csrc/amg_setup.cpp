@@ -249,7 +249,8 @@ void pair_plan(int n_rows, bool force_diag, const EnumRow& enum_row, std::vector
   }
 }
 
-double power_lambda(const HostBsr& A, const std::vector<double>& Dinv, const std::vector<uint8_t>& freem) {
+double power_lambda(const HostBsr& A, const std::vector<double>& Dinv, const std::vector<uint8_t>& freem,
+                    int steps) {
   const int b = A.br;
   const size_t N = (size_t)A.n * b;
   std::vector<double> v(N), y(N), t(b);
@@ -259,7 +260,7 @@ double power_lambda(const HostBsr& A, const std::vector<double>& Dinv, const std
     v[k] = freem[k] ? ((double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5) : 0.0;
   }
   double lam = 1.0;
-  for (int it = 0; it < 20; ++it) {
+  for (int it = 0; it < steps; ++it) {
     double nv = 0.0;
     for (double x : v) nv += x * x;
     nv = std::sqrt(nv);
@@ -324,7 +325,8 @@ void block_inverses(const HostBsr& A, std::vector<double>& Dinv) {
 
 void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
                         const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap, bool filter,
-                        std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow, bool exact_candidates) {
+                        std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow, bool exact_candidates,
+                        int power_steps) {
   levels.clear();
   levels.emplace_back();
   levels[0].A = A0;
@@ -435,7 +437,7 @@ void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, co
     }
     const HostBsr& As = filter ? Af : A;
     const std::vector<double>& Ds = filter ? Dinv_f : L.Dinv;
-    const double lam = power_lambda(As, Ds, L.free);
+    const double lam = power_lambda(As, Ds, L.free, std::max(1, power_steps));
     const double wP = 4.0 / (3.0 * std::max(lam, 1e-300));
     const int pb = b * NS;
     HostBsr P;

@@ -52,9 +52,11 @@ struct HostCoarse {
 // aggregate's QR (P_t B_c = B on the free unknowns); otherwise a column that
 // depends on the earlier ones within an aggregate is dropped with its
 // projections.
+// power_steps: steps of the power iteration that estimates lambda_max(D^-1 A)
+// for the prolongator smoothing weight 4 / (3 lambda).
 void build_sa_hierarchy(const HostBsr& A0, const std::vector<uint8_t>& free0, const double* X,
                         const std::vector<int32_t>& comp0, int coarse_max, int max_levels, int cap, bool filter,
                         std::vector<HostLevel>& levels, HostCoarse& coarse, bool grow = false,
-                        bool exact_candidates = false);
+                        bool exact_candidates = false, int power_steps = 20);
 
 }  // namespace fsi

@@ -206,7 +206,8 @@ void build_hierarchy(Handle& h, const std::vector<uint8_t>& free0, const std::ve
   HostCoarse hc;
   h.filter_p = h.opts.inertia_coef > 0.0;
   build_sa_hierarchy(A0, free0, X, comp0, std::max(1, h.opts.coarse_max_nodes), std::max(1, h.opts.max_levels),
-                     8, h.filter_p, hl, hc, h.opts.aggregation == FSI_AGG_GROW, h.opts.exact_candidates != 0);
+                     8, h.filter_p, hl, hc, h.opts.aggregation == FSI_AGG_GROW, h.opts.exact_candidates != 0,
+                     h.opts.power_steps);
   const int nl = (int)hl.size();
   const size_t ts = f32 ? 4 : 8;
   for (int l = 1; l < nl; ++l) {
@@ -758,6 +759,7 @@ static Handle* create_impl(const fsi_mesh_desc* mesh, int n_mat, const fsi_mater
     throw ArgError("unknown aggregation");
   if (h.opts.coarse_smoother != FSI_COARSE_JACOBI && h.opts.coarse_smoother != FSI_COARSE_MR)
     throw ArgError("unknown coarse smoother");
+  if (h.opts.power_steps < 1 || h.opts.power_steps > 10000) throw ArgError("power_steps must lie in [1, 10000]");
   // BiCGStab needs a fixed (linear) preconditioner
   if (h.opts.krylov == FSI_KRYLOV_BICGSTAB) h.opts.coarse_smoother = FSI_COARSE_JACOBI;
   h.opts.restart = std::min(std::max(h.opts.restart, 1), kMaxRestart);
@@ -1286,6 +1288,7 @@ void fsi_solid_default_opts(fsi_solver_opts* o) {
   o->autotune = 1;
   o->segment_krylov = 1;
   o->exact_candidates = 0;
+  o->power_steps = 20;
   o->coarse_max_nodes = 16;
   o->max_levels = 12;
   o->use_pspg = 1;

@@ -4,7 +4,7 @@
 // together with an FNV-1a hash over every level array, so that a test can
 // compare runs at different thread counts and check the products with scipy.
 //
-//   host_amg_setup_main <dir> <ring|grow> [exact] [filter]
+//   host_amg_setup_main <dir> <ring|grow> [exact] [filter] [steps=N]
 //
 // <dir>/dims.bin: int64 n, nb; rp.bin int32[n+1]; ci.bin int32[nb];
 // v.bin double[nb*16]; free.bin uint8[n*4]; X.bin double[n*3].
@@ -48,9 +48,12 @@ int main(int argc, char** argv) {
   const std::string d = argv[1];
   const bool grow = std::string(argv[2]) == "grow";
   bool exact = false, filter = false;
+  int steps = 20;
   for (int a = 3; a < argc; ++a) {
-    exact = exact || std::string(argv[a]) == "exact";
-    filter = filter || std::string(argv[a]) == "filter";
+    const std::string f = argv[a];
+    exact = exact || f == "exact";
+    filter = filter || f == "filter";
+    if (f.rfind("steps=", 0) == 0) steps = std::stoi(f.substr(6));
   }
   try {
     const auto dims = read_raw<int64_t>(d + "/dims.bin", 2);
@@ -66,7 +69,7 @@ int main(int argc, char** argv) {
     const std::vector<int32_t> comp(n, 0);
     std::vector<HostLevel> L;
     HostCoarse C;
-    build_sa_hierarchy(A, fr, X.data(), comp, 16, 12, 8, filter, L, C, grow, exact);
+    build_sa_hierarchy(A, fr, X.data(), comp, 16, 12, 8, filter, L, C, grow, exact, steps);
     uint64_t h = 1469598103934665603ull;
     for (const auto& l : L) {
       h = fnv(l.A.rp, h); h = fnv(l.A.ci, h); h = fnv(l.A.v, h); h = fnv(l.free, h); h = fnv(l.Dinv, h);

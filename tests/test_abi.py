@@ -115,3 +115,16 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             "else:\n    print('LOADED')\n") % str(tmp_path)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300, cwd=str(tmp_path))
     assert "IMPORT-ERROR" in out.stdout and "libfsi_solid.so is missing" in out.stdout, out.stdout + out.stderr
+
+
+def test_bad_power_steps_is_rejected_before_gpu_work(lib):
+    """opts.power_steps outside [1, 10000] is an argument error found on the host."""
+    from paper_1312_5561_gb300 import binding as b
+    d, mats, keep = _one_tet_desc([0, 0, 0, 0], 1)
+    for steps in (0, 20000):
+        o = b.default_opts(power_steps=steps)
+        h = ctypes.c_void_p()
+        st = b.lib.fsi_solid_create(ctypes.byref(d), 1, mats, ctypes.byref(o), ctypes.byref(h))
+        assert st == -1 and not h.value
+        assert b"power_steps" in b.lib.fsi_solid_last_error(None)
+    assert b.default_opts().power_steps == 20 and b.default_opts().exact_candidates == 0
