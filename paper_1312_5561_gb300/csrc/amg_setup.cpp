@@ -6,7 +6,9 @@
 // modes of the displacement (3 translations, 3 rotations) and a constant
 // pressure, orthonormalised per aggregate (QR).  The tentative prolongator is
 // smoothed once by damped Jacobi, P = (I - w D^-1 A) P_t with
-// w = 4 / (3 lambda_max(D^-1 A)), and the coarse operators are the Galerkin
+// w = 4 / (3 lambda), lambda a power-iteration estimate of lambda_max(D^-1 A)
+// (power_steps steps; a few tens of steps fall short of lambda_max where the
+// top eigenvalues cluster), and the coarse operators are the Galerkin
 // products P^T A P.  What stays fixed per mesh is computed here: the
 // aggregates, P_t, w, and the sparsity patterns of P, A P and P^T A P
 // together with the index plans of those products (the value loops run on
