@@ -193,3 +193,29 @@ def test_bench_default_is_the_documented_headline_configuration():
     tube = bench.make_parser().parse_args(["--config", "tube"])
     assert bench._workload_geometry(tube) == (64, 8, 128, 1.0e3)
     assert bench.solver_options(tube)["aggregation"] == 0
+
+
+def test_batched_segment_parameters_follow_the_recipe():
+    """Per segment of the seed-4 recipe: n_theta = 32 below 5e4 tets, else 64;
+    n_z = max(2, round(n_e / (6 * 8 * n_theta))); one fibre angle in
+    [20, 70] deg used at +/- alpha in both layers; kappa = ratio * c10 of the
+    media for both layers with ratio in [1e2, 1e5]; the segment's pressure on
+    its own faces."""
+    mesh = batched_tubes(32, seed=4)
+    segs = mesh.meta["segments"]
+    for s, sg in enumerate(segs):
+        em = mesh.seg_elem == s
+        n_e = int(em.sum())
+        assert sg["n_elems"] == n_e and sg["n_theta"] == (32 if n_e < 5.0e4 else 64)
+        assert n_e == 6 * 8 * sg["n_theta"] * sg["n_z"] and sg["n_z"] >= 2
+        assert 20.0 <= sg["alpha_deg"] <= 70.0 and 1.0e2 <= sg["kappa_ratio"] <= 1.0e5
+        a = mesh.fibre[em]
+        assert np.allclose(np.abs(a[:, :, 2]), np.sin(np.deg2rad(sg["alpha_deg"])), atol=1e-12)
+        mats = [mesh.materials[m] for m in np.unique(mesh.mat_id[em])]
+        assert len(mats) == 2 and all(m.kappa == mats[0].kappa for m in mats)
+        assert np.isclose(mats[0].kappa, sg["kappa_ratio"] * max(m.c10 for m in mats), rtol=1e-12)
+        assert np.allclose(mesh.face_pressure[mesh.seg_face == s], sg["pressure"])
+    # the draws spread over their ranges (32 segments)
+    alphas = np.array([sg["alpha_deg"] for sg in segs])
+    ratios = np.log10([sg["kappa_ratio"] for sg in segs])
+    assert alphas.max() - alphas.min() > 30.0 and ratios.max() - ratios.min() > 2.0
